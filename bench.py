@@ -1,0 +1,340 @@
+"""Benchmark of the coalesced-ghost translation step (one JSON line on rank 0).
+
+A step is one full translation step of the whole workload through the library: 27-cell
+block union and slot indexing, work list, the sweep kernel(s) (fused Ghost Translation
+tile kernel by default, or the 3-pass classical form), and the sparsity rule with FP64
+mass accounting.  Default workload: the uniform-mesh configuration, 64^3 periodic
+cells x 32^3 velocity cells (512 blocks of 4^3 per cell, 8.6e9 phase-space cells,
+34 GB of float32 f per copy), dt = 0.05 with dx = 1.
+
+Metric: phase-space cell updates per second (one update = one velocity cell of one
+spatial cell advanced through the full x->y->z step), whole job.  The state (34 GB)
+is far larger than L2 (129 MB), so no L2 flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the machine's host cores instead, on a
+bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_21450_gb300 import inputs  # noqa: E402
+
+METRIC = "phase-space cell updates/s (xyz)"
+UNIT = "updates/s"
+BYTES_PER_UPDATE = {"fused": 8.0, "3pass": 8.0}  # per launch: read f once, write once
+KERNEL = {"fused": "k_fused", "3pass": "k_pass"}
+LAUNCHES_PER_STEP = {"fused": 1, "3pass": 3}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the kernel
+    source as it is now (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(f"{kernel}:{workload}")
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2504_21450_gb300", "csrc", rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if h == rec.get("sha256_16") else None
+
+
+def cpu_baseline(cfg, budget_s=20.0):
+    """The FP64 oracle as it stands, on all host cores, on a 16^3 window of the workload
+    (the full velocity mesh), repeated until about budget_s of CPU work."""
+    import oracle
+    size = (16, 16, 16)
+    thr = inputs.threshold(cfg)
+    init = inputs.generate(cfg, size=size, thr=thr)
+    mesh = oracle.Mesh(n=size, nv=cfg.nv, vmin=cfg.vmin, dv=cfg.dv, dx=cfg.dx)
+    blk = oracle.as_blocks(init.off, init.ids, init.vals.astype(np.float64))
+    cores = oracle.max_threads()
+    updates, t0, reps = 0, time.perf_counter(), 0
+    while True:
+        oracle.step(mesh, blk, cfg.dt, thr, "xyz", nthreads=cores)
+        updates += blk.nblocks * 64
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s * 0.5 or reps >= 20:
+            break
+    el = time.perf_counter() - t0
+    return {"value": updates / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} step(s) of a periodic 16^3-cell window x {cfg.nv[0]}^3 velocity "
+                      f"cells ({blk.nblocks * 64:.3g} updates/step), FP64, OpenMP over block ids"}
+
+
+def run_reference(args, cfg):
+    """Reference arm: the FP64 oracle timed on the host cores, bounded window per step."""
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    thr = inputs.threshold(cfg)
+    # size the window so that the whole run stays within a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    edge = 16 if budget >= 3.0 else (12 if budget >= 1.2 else 8)
+    size = (edge, edge, edge)
+    init = inputs.generate(cfg, size=size, thr=thr)
+    mesh = oracle.Mesh(n=size, nv=cfg.nv, vmin=cfg.vmin, dv=cfg.dv, dx=cfg.dx)
+    blk = oracle.as_blocks(init.off, init.ids, init.vals.astype(np.float64))
+    cores = oracle.max_threads()
+    for _ in range(args.warmup):
+        blk = oracle.step(mesh, blk, cfg.dt, thr, "xyz", nthreads=cores)[0]
+    updates = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        updates += blk.nblocks * 64
+        blk = oracle.step(mesh, blk, cfg.dt, thr, "xyz", nthreads=cores)[0]
+    el = time.perf_counter() - t0
+    value = updates / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} cells x "
+                               f"{cfg.nv[0]}^3 velocity cells, periodic {edge}^3-cell window per step",
+                   "sample_cells": edge ** 3, "order": "xyz"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"periodic {edge}^3-cell window of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, cfg):
+    import torch
+    from paper_2504_21450_gb300 import vlasov
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    form = {"fused": vlasov.VL_FORM_FUSED, "3pass": vlasov.VL_FORM_3PASS}[args.form]
+
+    off, ids, vals, thr = inputs.generate_torch(cfg, f"cuda:{local}")
+    g = vlasov.Grid(cfg.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, device=local)
+    g.set_blocks(off, ids, vals)
+    host = None
+    if args.e2e:
+        host = (off.cpu().pin_memory(), ids.to(torch.int16).cpu().pin_memory(), vals.cpu().pin_memory())
+    del off, ids, vals
+    torch.cuda.empty_cache()
+
+    blocks = g.block_count()
+    for _ in range(args.warmup):
+        g.translate(cfg.dt, args.order, 1, form)
+        blocks = g.stats().blocks
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    updates = 0
+    sweep_ms = 0.0
+    launches = 0
+    phases = {"index_ms": 0.0, "sweep_ms": 0.0, "prune_ms": 0.0}
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            updates += blocks * 64
+            g.translate(cfg.dt, args.order, 1, form)
+            s = g.stats()
+            blocks = s.blocks
+            sweep_ms += s.sweep_ms
+            launches += s.launches
+            for k in phases:
+                phases[k] += getattr(s, k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    el_ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([el_ms, float(updates)], dtype=torch.float64, device="cuda")
+    if dist:
+        tm = t.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        t = tm
+    el_ms, total_updates = float(t[0]), float(t[1])
+    value = total_updates / (el_ms / 1e3)
+
+    # end to end through the public API with host buffers: H2D of the state, one step,
+    # D2H of the step's result (mass and block counters)
+    e2e = None
+    if args.e2e and host is not None:
+        h_off, h_ids, h_vals = host
+        nb = int(h_vals.shape[0])
+        e_steps = max(1, min(args.steps, 3))
+        e_updates = 0
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            vlasov.vl_set_blocks(g.handle, nb, h_off.data_ptr(), h_ids.data_ptr(), h_vals.data_ptr(), 0)
+            e_updates += nb * 64
+            g.translate(cfg.dt, args.order, 1, form)
+            _ = g.stats().mass
+        torch.cuda.synchronize()
+        e_el = time.perf_counter() - t0
+        if dist:
+            te = torch.tensor([e_el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e_el = float(te[0])
+        h2d = h_off.numel() * 8 + h_ids.numel() * 2 + h_vals.numel() * 4
+        e2e = {"value": e_updates * world / e_el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 56 + 8, "steps": e_steps}
+
+    peak, peak_kind = measured_peak_hbm()
+    launches_sweep = LAUNCHES_PER_STEP[args.form] * args.steps
+    per_launch_updates = updates / args.steps  # every sweep launch touches every update once
+    avg_launch_s = (sweep_ms / launches_sweep) / 1e3 if sweep_ms > 0 else float("nan")
+    achieved = BYTES_PER_UPDATE[args.form] * per_launch_updates / avg_launch_s / 1e9
+    workload = f"{cfg.name}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "kernel": KERNEL[args.form],
+                "traffic": traffic_for(KERNEL[args.form], workload),
+                "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[args.form] * per_launch_updates,
+                "avg_launch_ms": avg_launch_s * 1e3}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} periodic cells x "
+                               f"{cfg.nv[0]}x{cfg.nv[1]}x{cfg.nv[2]} velocity cells (4^3 blocks), "
+                               f"dt={cfg.dt}, rel. threshold {cfg.rel_threshold:g}",
+                   "form": args.form, "order": args.order, "parallelism": f"replicas{world}",
+                   "l2": "state (34 GB per copy) larger than L2; no flush",
+                   "blocks_per_step": updates / args.steps / 64},
+        "roofline": roofline,
+        "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fused", choices=["fused", "3pass"])
+    ap.add_argument("--config", default="uniform", choices=sorted(inputs.CONFIGS))
+    ap.add_argument("--order", default="xyz")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = inputs.CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

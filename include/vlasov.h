@@ -1,0 +1,190 @@
+/*
+ * vlasov.h -- C ABI of libvlgt, a single-GPU (GB300, sm_103a) implementation of the
+ * spatial translation step of a 6D Vlasov solver in its coalesced-ghost form.
+ *
+ * What the library computes (arXiv:2504.21450, "Coalescing MPI communication in 6D
+ * Vlasov simulations: solving ghost domains in Vlasiator"):
+ *   - Section 2 / Eq. 1: the v . grad_x f term of the Vlasov equation, advanced by three
+ *     Cartesian shears per time step (Section 2.1), each a mass-conserving
+ *     semi-Lagrangian remap with a piecewise-parabolic fit on a stencil of 2 cells that
+ *     writes into the cell itself and its downwind face neighbour; dt is limited so that
+ *     one face neighbour suffices (|v_d| dt / dx_d <= 1).
+ *   - Section 2: a sparse velocity space of 4x4x4 (64-value) blocks per spatial cell,
+ *     added where a neighbour can send content and removed below a sparsity threshold.
+ *   - Section 3: Ghost Translation -- each spatial tile loads its ghost halo once, wide
+ *     enough for all three sweeps, and computes on the ghost cells (the "fused" form),
+ *     instead of exchanging ghosts between sweeps (the classical, "3-pass" form).
+ *
+ * Conventions
+ *   - Spatial cell index c = x + nx*(y + ny*z); the grid is periodic in all dimensions.
+ *   - Block id b = bx + nbx*(by + nby*bz) with nbx = nv[0]/4 etc. (at most 65536 ids).
+ *   - The 64 values of a block are ordered vx fastest, then vy, then vz.  Velocity cell
+ *     centres: v_d = vmin[d] + (i_d + 1/2) dv[d].
+ *   - Transfer format ("per-cell lists"): cell_offsets[ncells+1] (int64, prefix sums),
+ *     block_ids[nblocks] (uint16, strictly increasing within a cell), values[nblocks*64]
+ *     (float32).  The library stores f in its own layout and converts on set/get.
+ *   - Every call returns a vl_status; no call aborts, traps or exits.  After an error
+ *     vl_last_error() describes it.  A grid is used by one host thread at a time.
+ *   - Work is queued on the grid's stream; calls that return data to the host
+ *     synchronise that stream.  Device pointers must be valid on the grid's device.
+ *   - Memory: the library owns the device memory of a grid and obtains it through the
+ *     caller's allocator callbacks (or cudaMalloc when they are NULL); the caller owns
+ *     every buffer it passes in.
+ */
+#ifndef VLASOV_H
+#define VLASOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vl_grid vl_grid; /* opaque, owned by the library */
+
+typedef enum {
+    VL_OK = 0,
+    VL_EINVAL = 1,     /* bad argument (null pointer, bad size, unsorted ids, ...) */
+    VL_ENOMEM = 2,     /* the allocator returned NULL */
+    VL_ECFL = 3,       /* max |v_d| dt / dx_d > 1 (Section 2.1's one-neighbour limit) */
+    VL_ECAPACITY = 4,  /* a pre-sized buffer was too small (recoverable) */
+    VL_ETIMEOUT = 5,   /* a bounded device wait ran out */
+    VL_ECUDA = 6,      /* a CUDA runtime call failed */
+    VL_ESTATE = 7      /* call not valid in the grid's current state */
+} vl_status;
+
+typedef enum {
+    VL_STORE_F32 = 0,          /* f stored as float32 */
+    VL_STORE_BF16_SCALED = 1,  /* bfloat16 per value x float32 scale per block */
+    VL_STORE_F16_SCALED = 2    /* float16 per value x float32 scale per block */
+} vl_storage;
+
+typedef enum {
+    VL_FORM_FUSED = 0,  /* Ghost Translation: one tile+halo load, x->y->z in one kernel */
+    VL_FORM_3PASS = 1,  /* classical: one HBM round trip per sweep direction */
+    VL_FORM_AUTO = 2    /* pick per workload (autotuner cache) */
+} vl_form;
+
+/* Spatial box: n cells per dimension, cell size dx, origin x0 (periodic). */
+typedef struct {
+    int n[3];
+    double dx[3];
+    double x0[3];
+} vl_space_desc;
+
+/* Velocity mesh: nv cells per dimension (multiples of block[d]), lower corner vmin,
+ * cell size dv; block must be {4,4,4} (Section 2's 64-element blocks). */
+typedef struct {
+    int nv[3];
+    double vmin[3];
+    double dv[3];
+    int block[3];
+} vl_vmesh_desc;
+
+/* Device memory and stream.  alloc/free may be NULL (then cudaMalloc/cudaFree are
+ * used).  alloc must return memory aligned to at least 256 bytes.  stream is a
+ * cudaStream_t (NULL: the legacy default stream); device is the CUDA device ordinal. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+    void* stream;
+    int device;
+} vl_device;
+
+/* Options of vl_translate; a NULL pointer means all defaults (the zero-initialised
+ * struct is NOT the default: use vl_translate_opts_default). */
+typedef struct {
+    int form;       /* vl_form; default VL_FORM_FUSED */
+    int limiter;    /* 1 (default): monotonicity limiter on; 0: linear PPM (dense
+                       velocity meshes only: without the limiter content can reach
+                       cells outside the 27-cell block union) */
+    int ghost;      /* ghost-layer depth k of GT-k; only 3 (exact) is implemented */
+    int tile[2];    /* fused tile extent along the first two sweep axes; 0 = default */
+    int check;      /* 1: synchronise after the call and report device-side errors */
+    int reserved[8];
+} vl_translate_opts;
+
+/* Counters of the last vl_translate call (FP64 sums on the device). */
+typedef struct {
+    int64_t steps;          /* steps done by the last call */
+    int64_t blocks;         /* blocks present after the last step */
+    int64_t union_blocks;   /* blocks of the last step's 27-cell union (before pruning) */
+    int64_t dropped_blocks; /* blocks removed by the sparsity rule in the last step */
+    double mass;            /* total mass after the last step (kept blocks) */
+    double dropped_mass;    /* mass removed by the sparsity rule over the whole call */
+    double mass_before;     /* total mass before the first step of the call */
+    double device_ms;       /* device time of the call's steps (CUDA events) */
+    double sweep_ms;        /* device time of the sweep kernels alone (the hot loop) */
+    double index_ms;        /* block union, slot indexing and work lists */
+    double prune_ms;        /* sparsity rule and dropped-mass accounting */
+    int64_t launches;       /* kernels the library launched during the call */
+} vl_step_stats;
+
+void vl_translate_opts_default(vl_translate_opts* opts);
+
+/* Create an empty grid (no blocks).  sparsity_threshold is absolute: after each step
+ * a block is kept iff its largest value is >= the threshold (Section 2); 0 keeps every
+ * block that the union created.  Only VL_STORE_F32 is accepted so far.
+ * Errors: VL_EINVAL (bad descriptor, block != {4,4,4}, storage), VL_ECUDA, VL_ENOMEM. */
+vl_status vl_grid_create(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
+                         double sparsity_threshold, vl_storage storage,
+                         const vl_device* device, vl_grid** out);
+
+/* Free the grid and all device memory it holds.  NULL is accepted. */
+vl_status vl_grid_destroy(vl_grid* grid);
+
+/* Replace the grid's state by the given per-cell lists.  on_device = 0: host pointers
+ * (copied synchronously); 1: device pointers on the grid's device (read on its stream
+ * before the call returns).  nblocks = cell_offsets[ncells].
+ * Errors: VL_EINVAL (offsets not non-decreasing, ids out of range or not strictly
+ * increasing within a cell), VL_ENOMEM, VL_ECUDA. */
+vl_status vl_set_blocks(vl_grid* grid, int64_t nblocks, const int64_t* cell_offsets,
+                        const uint16_t* block_ids, const float* values, int on_device);
+
+/* Number of blocks currently present (synchronises the grid's stream). */
+vl_status vl_get_block_count(vl_grid* grid, int64_t* nblocks);
+
+/* Copy the state out as per-cell lists into caller-allocated buffers of at least
+ * `capacity` blocks (cell_offsets: ncells+1 entries).  on_device as in vl_set_blocks.
+ * Errors: VL_ECAPACITY when capacity < vl_get_block_count. */
+vl_status vl_get_blocks(vl_grid* grid, int64_t capacity, int64_t* cell_offsets,
+                        uint16_t* block_ids, float* values, int on_device);
+
+/* Per-cell lists of a box window: the cells origin[d] + [0, size[d]) (wrapping
+ * periodically), x fastest, 1 <= size[d] <= n[d].  Same formats, ownership and errors as
+ * vl_get_blocks; cell_offsets has size[0]*size[1]*size[2]+1 entries.  Used to sample a
+ * large state (checkpointing a sub-domain, comparing a window with a reference). */
+vl_status vl_get_block_count_window(vl_grid* grid, const int origin[3], const int size[3],
+                                    int64_t* nblocks);
+vl_status vl_get_blocks_window(vl_grid* grid, const int origin[3], const int size[3],
+                               int64_t capacity, int64_t* cell_offsets, uint16_t* block_ids,
+                               float* values, int on_device);
+
+/* Advance the state by nsteps translation steps of length dt with the sweeps in the
+ * given order (a permutation of "xyz"; Section 2.1 uses z->x->y).  Each step: 27-cell
+ * block union, the three PPM shears (fused GT3 tile kernel or three passes), then the
+ * sparsity rule with FP64 accounting of the dropped mass.
+ * Errors: VL_ECFL (Section 2.1's one-neighbour limit), VL_EINVAL, VL_ENOMEM, VL_ECUDA. */
+vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
+                       const vl_translate_opts* opts);
+
+/* Velocity moments per cell (particle mass 1), FP64: out[c*7 + k] for
+ * k = n, nVx, nVy, nVz, Pxx, Pyy, Pzz with n = sum f dv^3, nV_d = sum v_d f dv^3,
+ * P_dd = sum (v_d - V_d)^2 f dv^3.  on_device as in vl_set_blocks. */
+vl_status vl_moments(vl_grid* grid, double* out, int on_device);
+
+/* FP64 total mass (sum f dx^3 dv^3) of the current state (synchronises). */
+vl_status vl_mass(vl_grid* grid, double* mass);
+
+/* Counters of the last vl_translate (synchronises). */
+vl_status vl_stats(vl_grid* grid, vl_step_stats* stats);
+
+const char* vl_status_str(vl_status status);
+const char* vl_last_error(const vl_grid* grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VLASOV_H */

@@ -1,0 +1,168 @@
+// common.cuh -- data layout and device helpers shared by the CUDA kernels of libvlgt.
+//
+// Phase-space layout in HBM (one "layout" = one state of the sparse velocity space):
+//   * For every block id b, a bitmap over the spatial cells, row by row: row = y + ny*z,
+//     W = ceil(nx/64) 64-bit words per row, bit x%64 of word x/64.
+//       ubits[b][row*W + w]  a slot exists for (cell, b) in this layout
+//       kbits[b][row*W + w]  the block is present (kept); always a subset of ubits
+//     The rank of a cell among the set ubits bits of segment b is its slot:
+//       rank = woff[b][row*W + w] + popc(ubits word & bits below x)
+//     (a collision-free, O(1) hash of (cell, block id) into the pool).
+//   * The values of segment b are stored block-id-major and velocity-chunk-major: the
+//     64 values of a block are 4 chunks of 16 (one vz plane of the 4x4x4 block each,
+//     vx fastest), and chunk q of the block with rank r sits at float offset
+//       (base[b]*4 + q*cnt[b] + r) * 16.
+//     A row of cells that all hold block b is therefore one contiguous run of 64-byte
+//     chunks per q, which keeps the 16-byte vector loads of a tile row coalesced.
+//   * dense[b]: bit 0 = every cell has a slot for b (rank = cell index), bit 1 = every
+//     cell holds b (kbits all set); sweeps skip the bitmaps when both are set.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vlgt {
+
+constexpr int kChunk = 16;   // values per velocity chunk (one vz plane of a block)
+constexpr int kHalo = 3;     // ghost depth of GT3: stencil 2 + one face neighbour
+
+struct LayoutView {
+    const uint64_t* ubits;
+    const uint64_t* kbits;
+    const uint32_t* woff;
+    const uint32_t* cnt;
+    const int64_t* base;
+    const uint8_t* dense;
+    float* pool;
+};
+
+struct GridGeom {
+    int n[3];      // nx, ny, nz
+    int W;         // words per row
+    int64_t R;     // rows = ny*nz
+    int64_t RW;    // words per segment
+    int64_t N;     // cells
+    int nb;        // block ids
+    int nbx, nby;  // block grid along vx, vy
+};
+
+// Per-velocity-cell constants of one sweep.  With c the Courant number v_d dt/dx_d and
+// g = |c|, the mass leaving a cell through its downwind face is
+//     out = g a + A minmod(d1, 2 d0) + B minmod(d0, 2 d1)
+// where d0 = a - aL and d1 = aR - a are the (face-clamped) distances of the cell's
+// edge values from its average.  This is the Colella-Woodward flux integral of the
+// limited parabola rewritten in the edge distances (A, B follow from expanding the
+// integral; for c < 0 the roles of the two faces swap).  up = 1 when content moves
+// towards higher indices (inflow comes from the lower neighbour).
+struct SweepConst {
+    float g, A, B;
+    int up;
+};
+
+__host__ __device__ inline SweepConst sweep_const(double c)
+{
+    SweepConst k;
+    if (c >= 0.0) {
+        k.g = (float)c;
+        k.A = (float)(c * (1.0 - c) * (1.0 - c));
+        k.B = (float)(c * c * (1.0 - c));
+        k.up = 1;
+    } else {
+        double g = -c;
+        k.g = (float)g;
+        k.A = (float)(-g * g * (1.0 - g));
+        k.B = (float)(-g * (1.0 - g) * (1.0 - g));
+        k.up = 0;
+    }
+    return k;
+}
+
+// median of (x, y, 0).  It is the minmod of x and y (0 when their signs differ, else
+// the one of smaller magnitude), and it is also x clamped into [min(0,y), max(0,y)].
+__device__ __forceinline__ float med0(float x, float y)
+{
+    return fmaxf(fminf(x, y), fminf(fmaxf(x, y), 0.0f));
+}
+
+// Sign-generic PPM remap of one line, one cell average pushed per call.  After the
+// value of cell p is pushed, the new average of cell p-3 is returned (the 7-cell
+// dependence window p-6..p).  Face values, limiter and flux follow the oracle's
+// reading of the paper (Colella-Woodward 1984 with a face value clamped between its
+// two cells), evaluated in FP32 in difference form:
+//   delta_j = a_{j+1} - a_j
+//   e_j     = face_{j+1/2} - a_j = delta_j/2 + (delta_{j-1} - delta_{j+1})/12
+//   d1_j    = e_j clamped into [min(0,delta_j), max(0,delta_j)]   (= aR_j - a_j)
+//   d0_{j+1}= delta_j - d1_j                                       (= a_{j+1} - aL_{j+1})
+// The CW84 limiter in these variables is d0' = minmod(d0, 2 d1), d1' = minmod(d1, 2 d0).
+template <bool kLimiter>
+struct Slide {
+    float a1, a2, a3;  // a_{p-1}, a_{p-2}, a_{p-3}
+    float l1, l2;      // delta_{p-2}, delta_{p-3}
+    float d0;          // d0_{p-2}
+    float o3, o4;      // out_{p-3}, out_{p-4}
+
+    __device__ __forceinline__ void reset()
+    {
+        a1 = a2 = a3 = l1 = l2 = d0 = o3 = o4 = 0.0f;
+    }
+
+    __device__ __forceinline__ float push(float a, const SweepConst& k)
+    {
+        float dn = a - a1;                                  // delta_{p-1}
+        float e = fmaf(l2 - dn, 1.0f / 12.0f, 0.5f * l1);   // e_{p-2}
+        float out;
+        float d1;
+        if (kLimiter) {
+            d1 = med0(e, l1);                               // d1_{p-2}
+            float m1 = med0(d1, d0 + d0);
+            float m0 = med0(d0, d1 + d1);
+            out = fmaf(k.B, m0, fmaf(k.A, m1, k.g * a2));   // out_{p-2}
+        } else {
+            d1 = e;
+            out = fmaf(k.B, d0, fmaf(k.A, d1, k.g * a2));
+        }
+        float res = a3 - o3 + (k.up ? o4 : out);            // new average of cell p-3
+        d0 = l1 - d1;                                       // d0_{p-1}
+        a3 = a2;
+        a2 = a1;
+        a1 = a;
+        l2 = l1;
+        l1 = dn;
+        o4 = o3;
+        o3 = out;
+        return res;
+    }
+};
+
+// Slot (rank) of cell (x, row) of block id b in a layout, or -1 when the cell has no
+// slot.  With check_keep the cell must also hold the block (kbits).
+__device__ __forceinline__ int64_t cell_rank(const LayoutView& L, const GridGeom& G, int b,
+                                             int x, int64_t row, bool check_keep)
+{
+    uint8_t dn = L.dense[b];
+    if ((dn & 1) && (!check_keep || (dn & 2))) return row * G.n[0] + x;
+    int64_t wi = (int64_t)b * G.RW + row * G.W + (x >> 6);
+    uint64_t u = L.ubits[wi];
+    uint64_t bit = 1ull << (x & 63);
+    if (!(u & bit)) return -1;
+    if (check_keep && !(L.kbits[wi] & bit)) return -1;
+    return (int64_t)L.woff[wi] + __popcll(u & (bit - 1));
+}
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Device-side counters of one step (FP64 sums, block counts, error flags).
+struct StepCounters {
+    double mass;           // sum of all written averages (union layout)
+    double dropped_mass;   // sum over removed blocks
+    unsigned long long kept;
+    unsigned long long dropped;
+    unsigned long long work_next;  // persistent-kernel work counter
+    int error;
+    int pad;
+};
+
+}  // namespace vlgt

@@ -1,0 +1,113 @@
+// grid.h -- host-side state of a vl_grid and the launchers shared between the
+// translation units of libvlgt (internal; the public interface is include/vlasov.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "vlasov.h"
+
+namespace vlgt {
+
+// Device buffers of one layout (see common.cuh for what each array holds).
+struct Layout {
+    uint64_t* ubits = nullptr;   // [nb * RW]
+    uint64_t* kbits = nullptr;   // [nb * RW]
+    uint32_t* woff = nullptr;    // [nb * RW]
+    uint32_t* wcount = nullptr;  // [nb * RW] popcount of ubits per word (scan input)
+    uint32_t* cnt = nullptr;     // [nb]
+    int64_t* base = nullptr;     // [nb + 1]
+    uint8_t* dense = nullptr;    // [nb]
+    uint32_t* kcnt = nullptr;    // [nb] kept blocks per id
+    float* pool = nullptr;       // [capacity * 64]
+    uint8_t* keepq = nullptr;    // [capacity * 4] per-chunk keep flags of the last sweep
+    int64_t capacity = 0;        // blocks the pool can hold
+    int64_t total = 0;           // slots in use (host copy)
+
+    LayoutView view() const { return LayoutView{ubits, kbits, woff, cnt, base, dense, pool}; }
+};
+
+struct Grid {
+    vl_space_desc space;
+    vl_vmesh_desc vmesh;
+    double threshold = 0.0;
+    vl_storage storage = VL_STORE_F32;
+    vl_device dev;
+    cudaStream_t stream = nullptr;
+    GridGeom geom;
+    Layout lay[2];   // lay[cur] holds the state, lay[1-cur] the next step's
+    int cur = 0;
+    bool has_state = false;
+
+    // scratch
+    StepCounters* counters = nullptr;     // device
+    StepCounters* counters_host = nullptr;  // pinned
+    uint32_t* tile_flags = nullptr;       // [nb * ntiles]
+    uint32_t* tile_pos = nullptr;         // [nb * ntiles]
+    uint32_t* item_cnt = nullptr;         // [nb]
+    int64_t* item_base = nullptr;         // [nb + 1]
+    uint32_t* items = nullptr;            // [nb * ntiles]
+    double* item_mass = nullptr;          // [4 * nb * ntiles] (or per CTA of the 3-pass)
+    int64_t ntiles_alloc = 0;
+    int64_t item_mass_alloc = 0;
+    int64_t* host_scalar = nullptr;       // pinned
+
+    vl_step_stats stats{};
+    int64_t launches = 0;                 // kernels launched by the library (running count)
+    cudaEvent_t ev_sweep0 = nullptr, ev_sweep1 = nullptr;  // bracket the sweep kernels
+    std::string last_error;
+
+    void* alloc(size_t bytes);
+    void release(void* p);
+};
+
+// Running count of kernel launches made by the library (all grids of the process).
+void note_launch();
+int64_t launch_count();
+
+// Records msg as the grid's last error and returns st.
+vl_status fail(Grid* g, vl_status st, const std::string& msg);
+vl_status cuda_fail(Grid* g, cudaError_t e, const char* what);
+
+// ---- layout.cu -------------------------------------------------------------
+vl_status layout_alloc_meta(Grid* g, Layout& L);
+void layout_free(Grid* g, Layout& L);
+vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks);
+// Counts, offsets and dense flags of L from its ubits (woff, cnt, base, dense);
+// returns the total number of slots in *total (synchronises the stream).
+vl_status layout_index(Grid* g, Layout& L, int64_t* total);
+// next.ubits = 27-cell dilation of cur.kbits (periodic).
+void launch_union(Grid* g, const Layout& cur, Layout& next);
+// next.kbits from the per-chunk keep flags; counts kept/dropped blocks and the FP64
+// mass of dropped blocks into g->counters; sets next.dense bit 1 and next.kcnt.
+void launch_pack_keep(Grid* g, Layout& next);
+vl_status set_blocks(Grid* g, int64_t nblocks, const int64_t* off, const uint16_t* ids,
+                     const float* vals, int on_device);
+vl_status get_block_count(Grid* g, int64_t* n);
+vl_status get_blocks(Grid* g, int64_t capacity, int64_t* off, uint16_t* ids, float* vals,
+                     int on_device);
+vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capacity,
+                     int64_t* off_out, uint16_t* ids_out, float* vals_out, int on_device,
+                     int64_t* count);
+vl_status moments(Grid* g, double* out, int on_device);
+vl_status total_mass(Grid* g, double* mass);
+// Generic scans used by the layout code and the work lists.
+void launch_seg_scan(const uint32_t* in, uint32_t* out, uint32_t* seg_total, int64_t seg_len,
+                     int64_t nseg, cudaStream_t s);
+void launch_base_scan(const uint32_t* seg_total, int64_t* base, int64_t nseg, cudaStream_t s);
+
+// ---- fused.cu / sweep3.cu --------------------------------------------------
+struct StepArgs {
+    double c_scale[3];  // dt / dx_d
+    int order[3];       // physical axis of sweep j
+    int limiter;
+    int tile[2];
+};
+vl_status run_fused(Grid* g, const StepArgs& a);
+vl_status run_3pass(Grid* g, const StepArgs& a);
+vl_status fused_prepare(Grid* g, const StepArgs& a, int64_t* nwork);
+
+}  // namespace vlgt

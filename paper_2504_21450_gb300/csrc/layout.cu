@@ -1,0 +1,751 @@
+// layout.cu -- sparse velocity-space bookkeeping of libvlgt: block-set union (27-cell
+// dilation of the presence bitmaps), slot indexing (segmented scans), the sparsity rule
+// (keep flags -> presence bitmaps, FP64 dropped mass), conversion from and to per-cell
+// block lists, and FP64 velocity moments.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "grid.h"
+
+namespace vlgt {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of each segment of seg_len counts; one CTA per segment.
+__global__ void k_seg_scan(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                           uint32_t* __restrict__ seg_total, int64_t seg_len)
+{
+    __shared__ uint32_t wsum[32];
+    const int64_t seg = blockIdx.x;
+    const uint32_t* src = in + seg * seg_len;
+    uint32_t* dst = out + seg * seg_len;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t carry = 0;
+    for (int64_t start = 0; start < seg_len; start += blockDim.x) {
+        int64_t i = start + threadIdx.x;
+        uint32_t v = i < seg_len ? src[i] : 0u;
+        uint32_t x = warp_incl_scan(v, lane);
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < nw ? wsum[lane] : 0u;
+            w = warp_incl_scan(w, lane);
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        uint32_t pre = carry + (warp > 0 ? wsum[warp - 1] : 0u);
+        if (i < seg_len) dst[i] = pre + x - v;
+        carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) seg_total[seg] = carry;
+}
+
+// base[s] = sum of seg_total[0..s), base[nseg] = grand total (64-bit); one CTA.
+__global__ void k_base_scan(const uint32_t* __restrict__ seg_total, int64_t* __restrict__ base,
+                            int64_t nseg)
+{
+    __shared__ unsigned long long wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long carry = 0;
+    for (int64_t start = 0; start < nseg; start += blockDim.x) {
+        int64_t i = start + threadIdx.x;
+        unsigned long long v = i < nseg ? seg_total[i] : 0ull;
+        unsigned long long x = warp_incl_scan64(v, lane);
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = lane < nw ? wsum[lane] : 0ull;
+            w = warp_incl_scan64(w, lane);
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        unsigned long long pre = carry + (warp > 0 ? wsum[warp - 1] : 0ull);
+        if (i < nseg) base[i] = (int64_t)(pre + x - v);
+        carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) base[nseg] = (int64_t)carry;
+}
+
+__device__ __forceinline__ uint64_t word_mask(int nx, int w)
+{
+    int last = nx - 1;
+    if (w < (last >> 6)) return ~0ull;
+    int top = last & 63;
+    return top == 63 ? ~0ull : ((1ull << (top + 1)) - 1ull);
+}
+
+// One word of a row dilated by one cell along x with periodic wrap.
+__device__ __forceinline__ uint64_t xdilate(const uint64_t* row, int W, int nx, int w)
+{
+    uint64_t cur = row[w];
+    uint64_t prev = w > 0 ? row[w - 1] : 0ull;
+    uint64_t next = (w + 1 < W) ? row[w + 1] : 0ull;
+    uint64_t left = (cur << 1) | (prev >> 63);   // bit x receives bit x-1
+    uint64_t right = (cur >> 1) | (next << 63);  // bit x receives bit x+1
+    int last = nx - 1;
+    if (w == 0) left |= (row[last >> 6] >> (last & 63)) & 1ull;
+    if (w == (last >> 6)) right |= (row[0] & 1ull) << (last & 63);
+    return cur | left | right;
+}
+
+// next.ubits = union of cur.kbits over the 3x3x3 periodic neighbourhood (a block can
+// only arrive from a cell at most one step away along each axis, since |c| <= 1 per
+// sweep); next.wcount = popcount per word.
+__global__ void k_union(GridGeom G, const uint64_t* __restrict__ kin, uint64_t* __restrict__ uout,
+                        uint32_t* __restrict__ wcount)
+{
+    int64_t total = (int64_t)G.nb * G.RW;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = i / G.RW;
+        int64_t rw = i - b * G.RW;
+        int64_t row = rw / G.W;
+        int w = (int)(rw - row * G.W);
+        int y = (int)(row % G.n[1]);
+        int z = (int)(row / G.n[1]);
+        const uint64_t* seg = kin + b * G.RW;
+        uint64_t acc = 0;
+        for (int dz = -1; dz <= 1; dz++) {
+            int zz = wrapi(z + dz, G.n[2]);
+            for (int dy = -1; dy <= 1; dy++) {
+                int yy = wrapi(y + dy, G.n[1]);
+                const uint64_t* r = seg + ((int64_t)yy + (int64_t)G.n[1] * zz) * G.W;
+                acc |= xdilate(r, G.W, G.n[0], w);
+            }
+        }
+        acc &= word_mask(G.n[0], w);
+        uout[i] = acc;
+        wcount[i] = (uint32_t)__popcll(acc);
+    }
+}
+
+__global__ void k_dense_u(const uint32_t* __restrict__ cnt, uint8_t* __restrict__ dense, int nb,
+                          int64_t N)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) dense[b] = (cnt[b] == (uint32_t)N) ? 1 : 0;
+}
+
+__global__ void k_dense_k(const uint32_t* __restrict__ kcnt, uint8_t* __restrict__ dense, int nb,
+                          int64_t N)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb && kcnt[b] == (uint32_t)N) dense[b] |= 2;
+}
+
+constexpr int kPackThreads = 256;
+
+// Sparsity rule: a slot of the new layout stays iff any of its four chunks had a value
+// >= threshold (the per-chunk flags are written by the sweep epilogue).  Removed blocks
+// add their FP64 mass (sum of the 64 averages) to the dropped mass.
+__global__ void k_pack_keep(GridGeom G, LayoutView L, const uint8_t* __restrict__ keepq,
+                            uint64_t* __restrict__ kout, uint32_t* __restrict__ kcnt,
+                            StepCounters* __restrict__ ctr, int64_t chunks_per_seg)
+{
+    __shared__ unsigned long long s_kept[kPackThreads / 32], s_drop[kPackThreads / 32];
+    __shared__ double s_mass[kPackThreads / 32];
+    const int64_t b = blockIdx.x / chunks_per_seg;
+    const int64_t rw = (blockIdx.x % chunks_per_seg) * kPackThreads + threadIdx.x;
+    unsigned long long kept = 0, drop = 0;
+    double dmass = 0.0;
+    if (rw < G.RW) {
+        int64_t wi = b * G.RW + rw;
+        uint64_t u = L.ubits[wi];
+        uint64_t k = 0;
+        uint32_t wo = L.woff[wi];
+        int64_t bb = L.base[b];
+        uint32_t cb = L.cnt[b];
+        uint64_t rest = u;
+        while (rest) {
+            int bit = __ffsll((long long)rest) - 1;
+            rest &= rest - 1;
+            int64_t rank = (int64_t)wo + __popcll(u & ((1ull << bit) - 1ull));
+            int64_t slot = bb + rank;
+            uint32_t flags = *reinterpret_cast<const uint32_t*>(keepq + slot * 4);
+            if (flags) {
+                k |= 1ull << bit;
+                kept++;
+            } else {
+                drop++;
+                double s = 0.0;
+                for (int q = 0; q < 4; q++) {
+                    const float4* p = reinterpret_cast<const float4*>(
+                        L.pool + ((bb * 4 + (int64_t)q * cb + rank) * kChunk));
+                    for (int j = 0; j < 4; j++) {
+                        float4 v = p[j];
+                        s += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
+                    }
+                }
+                dmass += s;
+            }
+        }
+        kout[wi] = k;
+    }
+    // CTA reduction, one atomic per CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        kept += __shfl_down_sync(0xffffffffu, kept, o);
+        drop += __shfl_down_sync(0xffffffffu, drop, o);
+        dmass += __shfl_down_sync(0xffffffffu, dmass, o);
+    }
+    if (lane == 0) {
+        s_kept[warp] = kept;
+        s_drop[warp] = drop;
+        s_mass[warp] = dmass;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long K = 0, D = 0;
+        double M = 0.0;
+        for (int w = 0; w < kPackThreads / 32; w++) {
+            K += s_kept[w];
+            D += s_drop[w];
+            M += s_mass[w];
+        }
+        if (K) atomicAdd(&kcnt[b], (uint32_t)K);
+        if (K) atomicAdd(&ctr->kept, K);
+        if (D) atomicAdd(&ctr->dropped, D);
+        if (M != 0.0) atomicAdd(&ctr->dropped_mass, M);
+    }
+}
+
+// ---- per-cell lists -> layout ----------------------------------------------------
+__device__ __forceinline__ int64_t cell_of_block(const int64_t* off, int64_t N, int64_t t)
+{
+    int64_t lo = 0, hi = N;  // find c with off[c] <= t < off[c+1]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_check_offsets(const int64_t* __restrict__ off, int64_t N, int64_t M, int* err)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0 && (off[0] != 0 || off[N] != M)) atomicOr(err, 1);
+    if (c < N && off[c + 1] < off[c]) atomicOr(err, 1);
+}
+
+__global__ void k_mark(GridGeom G, const int64_t* __restrict__ off, const uint16_t* __restrict__ ids,
+                       int64_t M, uint64_t* __restrict__ ubits, int64_t* __restrict__ cell_of,
+                       int* err)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    int64_t c = cell_of_block(off, G.N, t);
+    int b = ids[t];
+    if (b >= G.nb) {
+        atomicOr(err, 2);
+        return;
+    }
+    if (t > off[c] && ids[t - 1] >= ids[t]) atomicOr(err, 4);
+    cell_of[t] = c;
+    int x = (int)(c % G.n[0]);
+    int64_t row = c / G.n[0];
+    atomicOr((unsigned long long*)&ubits[(int64_t)b * G.RW + row * G.W + (x >> 6)],
+             (unsigned long long)(1ull << (x & 63)));
+}
+
+__global__ void k_scatter(GridGeom G, LayoutView L, const uint16_t* __restrict__ ids,
+                          const int64_t* __restrict__ cell_of, const float* __restrict__ vals,
+                          int64_t M)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * 64) return;
+    int64_t t = i >> 6;
+    int v = (int)(i & 63);
+    int b = ids[t];
+    int64_t c = cell_of[t];
+    int x = (int)(c % G.n[0]);
+    int64_t rank = cell_rank(L, G, b, x, c / G.n[0], false);
+    int64_t dst = ((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15);
+    L.pool[dst] = vals[i];
+}
+
+// ---- layout -> per-cell lists ----------------------------------------------------
+struct Window {
+    int o[3], s[3];
+    int64_t ncell;
+};
+
+// global (x, row) of window cell wc (x fastest), wrapping periodically
+__device__ __forceinline__ void window_cell(const GridGeom& G, const Window& Wn, int64_t wc, int& x,
+                                            int64_t& row)
+{
+    int wx = (int)(wc % Wn.s[0]);
+    int64_t r = wc / Wn.s[0];
+    int wy = (int)(r % Wn.s[1]);
+    int wz = (int)(r / Wn.s[1]);
+    x = wrapi(Wn.o[0] + wx, G.n[0]);
+    int y = wrapi(Wn.o[1] + wy, G.n[1]);
+    int z = wrapi(Wn.o[2] + wz, G.n[2]);
+    row = y + (int64_t)G.n[1] * z;
+}
+
+__global__ void k_cell_counts(GridGeom G, Window Wn, const uint64_t* __restrict__ kbits,
+                              uint32_t* __restrict__ cnt)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Wn.ncell) return;
+    int x;
+    int64_t row;
+    window_cell(G, Wn, c, x, row);
+    int64_t wo = row * G.W + (x >> 6);
+    uint64_t bit = 1ull << (x & 63);
+    uint32_t k = 0;
+    for (int b = 0; b < G.nb; b++) k += (kbits[(int64_t)b * G.RW + wo] & bit) ? 1u : 0u;
+    cnt[c] = k;
+}
+
+__global__ void k_offsets64(const uint32_t* __restrict__ excl, const int64_t* __restrict__ chunk_base,
+                            int64_t chunk, int64_t N, int64_t* __restrict__ off)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) off[c] = chunk_base[c / chunk] + excl[c];
+    if (c == 0) off[N] = chunk_base[(N + chunk - 1) / chunk];
+}
+
+__global__ void k_fill_ids(GridGeom G, Window Wn, LayoutView L, const int64_t* __restrict__ off,
+                           uint16_t* __restrict__ ids, int64_t* __restrict__ rank_of)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Wn.ncell) return;
+    int x;
+    int64_t row;
+    window_cell(G, Wn, c, x, row);
+    int64_t wo = row * G.W + (x >> 6);
+    uint64_t bit = 1ull << (x & 63);
+    int64_t o = off[c];
+    for (int b = 0; b < G.nb; b++) {
+        if (L.kbits[(int64_t)b * G.RW + wo] & bit) {
+            ids[o] = (uint16_t)b;
+            rank_of[o] = cell_rank(L, G, b, x, row, false);
+            o++;
+        }
+    }
+}
+
+__global__ void k_gather(LayoutView L, const uint16_t* __restrict__ ids,
+                         const int64_t* __restrict__ rank_of, float* __restrict__ vals, int64_t M)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * 64) return;
+    int64_t t = i >> 6;
+    int v = (int)(i & 63);
+    int b = ids[t];
+    vals[i] = L.pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank_of[t]) * kChunk + (v & 15)];
+}
+
+// ---- moments -----------------------------------------------------------------------
+struct VMesh {
+    double vmin[3], dv[3];
+};
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// One warp per cell; two passes over the cell's blocks (n and nV, then P about V).
+__global__ void k_moments(GridGeom G, LayoutView L, VMesh V, double* __restrict__ out)
+{
+    int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (c >= G.N) return;
+    int x = (int)(c % G.n[0]);
+    int64_t row = c / G.n[0];
+    int64_t wo = row * G.W + (x >> 6);
+    uint64_t bit = 1ull << (x & 63);
+    double dv3 = V.dv[0] * V.dv[1] * V.dv[2];
+    double s0 = 0, s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+    double Vd[3] = {0, 0, 0};
+    for (int pass = 0; pass < 2; pass++) {
+        for (int b0 = 0; b0 < G.nb; b0 += 32) {
+            int bl = b0 + lane;
+            bool has = bl < G.nb && (L.kbits[(int64_t)bl * G.RW + wo] & bit);
+            unsigned m = __ballot_sync(0xffffffffu, has);
+            while (m) {
+                int j = __ffs(m) - 1;
+                m &= m - 1;
+                int b = b0 + j;
+                int64_t rank = cell_rank(L, G, b, x, row, false);
+                int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+                for (int h = 0; h < 2; h++) {
+                    int v = lane + 32 * h;
+                    float f = L.pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15)];
+                    double vel[3] = {V.vmin[0] + (bx * 4 + (v & 3) + 0.5) * V.dv[0],
+                                     V.vmin[1] + (by * 4 + ((v >> 2) & 3) + 0.5) * V.dv[1],
+                                     V.vmin[2] + (bz * 4 + (v >> 4) + 0.5) * V.dv[2]};
+                    if (pass == 0) {
+                        s0 += f;
+                        for (int d = 0; d < 3; d++) s1[d] += vel[d] * f;
+                    } else {
+                        for (int d = 0; d < 3; d++) s2[d] += (vel[d] - Vd[d]) * (vel[d] - Vd[d]) * f;
+                    }
+                }
+            }
+        }
+        if (pass == 0) {
+            s0 = warp_sum(s0);
+            for (int d = 0; d < 3; d++) s1[d] = warp_sum(s1[d]);
+            for (int d = 0; d < 3; d++) Vd[d] = s0 != 0.0 ? s1[d] / s0 : 0.0;
+        }
+    }
+    for (int d = 0; d < 3; d++) s2[d] = warp_sum(s2[d]);
+    if (lane == 0) {
+        double* o = out + c * 7;
+        o[0] = s0 * dv3;
+        for (int d = 0; d < 3; d++) o[1 + d] = s1[d] * dv3;
+        for (int d = 0; d < 3; d++) o[4 + d] = s2[d] * dv3;
+    }
+}
+
+__global__ void k_popcount(const uint64_t* __restrict__ u, uint32_t* __restrict__ c, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = (uint32_t)__popcll(u[i]);
+}
+
+__global__ void k_sum_density(const double* __restrict__ mom, int64_t N, double* __restrict__ out)
+{
+    double s = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x)
+        s += mom[c * 7];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+void launch_seg_scan(const uint32_t* in, uint32_t* out, uint32_t* seg_total, int64_t seg_len,
+                     int64_t nseg, cudaStream_t s)
+{
+    if (nseg <= 0) return;
+    int threads = seg_len >= 1024 ? kScanThreads : (seg_len >= 256 ? 256 : 64);
+    k_seg_scan<<<(unsigned)nseg, threads, 0, s>>>(in, out, seg_total, seg_len); note_launch();
+}
+
+void launch_base_scan(const uint32_t* seg_total, int64_t* base, int64_t nseg, cudaStream_t s)
+{
+    k_base_scan<<<1, kScanThreads, 0, s>>>(seg_total, base, nseg); note_launch();
+}
+
+vl_status layout_alloc_meta(Grid* g, Layout& L)
+{
+    const GridGeom& G = g->geom;
+    size_t words = (size_t)G.nb * (size_t)G.RW;
+    L.ubits = (uint64_t*)g->alloc(words * 8);
+    L.kbits = (uint64_t*)g->alloc(words * 8);
+    L.woff = (uint32_t*)g->alloc(words * 4);
+    L.wcount = (uint32_t*)g->alloc(words * 4);
+    L.cnt = (uint32_t*)g->alloc((size_t)G.nb * 4);
+    L.base = (int64_t*)g->alloc(((size_t)G.nb + 1) * 8);
+    L.dense = (uint8_t*)g->alloc((size_t)G.nb);
+    L.kcnt = (uint32_t*)g->alloc((size_t)G.nb * 4);
+    if (!L.ubits || !L.kbits || !L.woff || !L.wcount || !L.cnt || !L.base || !L.dense || !L.kcnt)
+        return fail(g, VL_ENOMEM, "allocation of the block bitmaps failed");
+    cudaMemsetAsync(L.ubits, 0, words * 8, g->stream);
+    cudaMemsetAsync(L.kbits, 0, words * 8, g->stream);
+    cudaMemsetAsync(L.dense, 0, (size_t)G.nb, g->stream);
+    return VL_OK;
+}
+
+void layout_free(Grid* g, Layout& L)
+{
+    g->release(L.ubits);
+    g->release(L.kbits);
+    g->release(L.woff);
+    g->release(L.wcount);
+    g->release(L.cnt);
+    g->release(L.base);
+    g->release(L.dense);
+    g->release(L.kcnt);
+    g->release(L.pool);
+    g->release(L.keepq);
+    L = Layout{};
+}
+
+vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks)
+{
+    if (blocks <= L.capacity && L.pool) return VL_OK;
+    int64_t cap = blocks + blocks / 8 + 64;
+    g->release(L.pool);
+    g->release(L.keepq);
+    L.pool = (float*)g->alloc((size_t)cap * 64 * sizeof(float));
+    L.keepq = (uint8_t*)g->alloc((size_t)cap * 4);
+    if (!L.pool || !L.keepq) {
+        L.capacity = 0;
+        return fail(g, VL_ENOMEM, "allocation of the phase-space pool failed (" +
+                                      std::to_string(cap * 256) + " bytes)");
+    }
+    L.capacity = cap;
+    return VL_OK;
+}
+
+vl_status layout_index(Grid* g, Layout& L, int64_t* total)
+{
+    const GridGeom& G = g->geom;
+    launch_seg_scan(L.wcount, L.woff, L.cnt, G.RW, G.nb, g->stream);
+    launch_base_scan(L.cnt, L.base, G.nb, g->stream);
+    k_dense_u<<<nblk(G.nb, 256), 256, 0, g->stream>>>(L.cnt, L.dense, G.nb, G.N); note_launch();
+    cudaMemcpyAsync(g->host_scalar, L.base + G.nb, 8, cudaMemcpyDeviceToHost, g->stream);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "layout index");
+    *total = g->host_scalar[0];
+    L.total = *total;
+    return VL_OK;
+}
+
+void launch_union(Grid* g, const Layout& cur, Layout& next)
+{
+    const GridGeom& G = g->geom;
+    int64_t total = (int64_t)G.nb * G.RW;
+    int blocks = (int)std::min<int64_t>(nblk(total, 256), 152 * 32);
+    k_union<<<blocks, 256, 0, g->stream>>>(G, cur.kbits, next.ubits, next.wcount); note_launch();
+}
+
+void launch_pack_keep(Grid* g, Layout& next)
+{
+    const GridGeom& G = g->geom;
+    int64_t cps = (G.RW + kPackThreads - 1) / kPackThreads;
+    cudaMemsetAsync(next.kcnt, 0, (size_t)G.nb * 4, g->stream);
+    k_pack_keep<<<(unsigned)(cps * G.nb), kPackThreads, 0, g->stream>>>(
+        G, next.view(), next.keepq, next.kbits, next.kcnt, g->counters, cps); note_launch();
+    k_dense_k<<<nblk(G.nb, 256), 256, 0, g->stream>>>(next.kcnt, next.dense, G.nb, G.N); note_launch();
+}
+
+namespace {
+struct Scratch {
+    Grid* g;
+    std::vector<void*> ptrs;
+    explicit Scratch(Grid* gg) : g(gg) {}
+    void* get(size_t bytes)
+    {
+        void* p = g->alloc(bytes);
+        if (p) ptrs.push_back(p);
+        return p;
+    }
+    ~Scratch()
+    {
+        // frees are stream-ordered for the caching allocator; synchronise first so that
+        // no kernel still reads a buffer handed back to cudaFree-based allocators
+        cudaStreamSynchronize(g->stream);
+        for (void* p : ptrs) g->release(p);
+    }
+};
+}  // namespace
+
+vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* ids_in,
+                     const float* vals_in, int on_device)
+{
+    const GridGeom& G = g->geom;
+    cudaStream_t s = g->stream;
+    if (M < 0 || !off_in || (M > 0 && (!ids_in || !vals_in)))
+        return fail(g, VL_EINVAL, "vl_set_blocks: null pointer or negative block count");
+    Scratch sc(g);
+    const int64_t* off = off_in;
+    const uint16_t* ids = ids_in;
+    const float* vals = vals_in;
+    if (!on_device) {
+        int64_t* d_off = (int64_t*)sc.get((size_t)(G.N + 1) * 8);
+        uint16_t* d_ids = (uint16_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 2);
+        float* d_vals = (float*)sc.get((size_t)std::max<int64_t>(M, 1) * 256);
+        if (!d_off || !d_ids || !d_vals) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
+        cudaMemcpyAsync(d_off, off_in, (size_t)(G.N + 1) * 8, cudaMemcpyHostToDevice, s);
+        if (M > 0) {
+            cudaMemcpyAsync(d_ids, ids_in, (size_t)M * 2, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_vals, vals_in, (size_t)M * 256, cudaMemcpyHostToDevice, s);
+        }
+        off = d_off;
+        ids = d_ids;
+        vals = d_vals;
+    }
+    Layout& L = g->lay[g->cur];
+    size_t words = (size_t)G.nb * (size_t)G.RW;
+    int64_t* cell_of = (int64_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 8);
+    int* err = (int*)sc.get(sizeof(int));
+    if (!cell_of || !err) return fail(g, VL_ENOMEM, "vl_set_blocks: scratch allocation failed");
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    cudaMemsetAsync(L.ubits, 0, words * 8, s);
+    k_check_offsets<<<nblk(G.N + 1, 256), 256, 0, s>>>(off, G.N, M, err); note_launch();
+    if (M > 0) { k_mark<<<nblk(M, 256), 256, 0, s>>>(G, off, ids, M, L.ubits, cell_of, err); note_launch(); }
+    cudaMemcpyAsync(g->host_scalar, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks");
+    int herr = (int)(g->host_scalar[0] & 0xffffffff);
+    if (herr & 1) return fail(g, VL_EINVAL, "vl_set_blocks: cell offsets must start at 0, be non-decreasing and end at nblocks");
+    if (herr & 2) return fail(g, VL_EINVAL, "vl_set_blocks: block id out of range of the velocity mesh");
+    if (herr & 4) return fail(g, VL_EINVAL, "vl_set_blocks: block ids must be strictly increasing within a cell");
+    k_popcount<<<nblk((int64_t)words, 256), 256, 0, s>>>(L.ubits, L.wcount, (int64_t)words); note_launch();
+    cudaMemcpyAsync(L.kbits, L.ubits, words * 8, cudaMemcpyDeviceToDevice, s);
+    int64_t total = 0;
+    vl_status st = layout_index(g, L, &total);
+    if (st != VL_OK) return st;
+    if (total != M) return fail(g, VL_EINVAL, "vl_set_blocks: duplicate block ids");
+    k_dense_k<<<nblk(G.nb, 256), 256, 0, s>>>(L.cnt, L.dense, G.nb, G.N); note_launch();
+    st = layout_ensure_pool(g, L, std::max<int64_t>(M, 1));
+    if (st != VL_OK) return st;
+    if (M > 0) { k_scatter<<<nblk(M * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, vals, M); note_launch(); }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks scatter");
+    g->has_state = true;
+    return VL_OK;
+}
+
+namespace {
+Window make_window(const GridGeom& G, const int* origin, const int* size)
+{
+    Window Wn;
+    Wn.ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        Wn.o[d] = origin ? origin[d] : 0;
+        Wn.s[d] = size ? size[d] : G.n[d];
+        Wn.ncell *= Wn.s[d];
+    }
+    return Wn;
+}
+}  // namespace
+
+// Per-cell lists of a box window of the grid (the whole grid when origin/size are
+// NULL).  With count_only, only *count is produced.
+vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capacity,
+                     int64_t* off_out, uint16_t* ids_out, float* vals_out, int on_device,
+                     int64_t* count)
+{
+    const GridGeom& G = g->geom;
+    const Layout& L = g->lay[g->cur];
+    cudaStream_t s = g->stream;
+    if (size)
+        for (int d = 0; d < 3; d++)
+            if (size[d] <= 0 || size[d] > G.n[d])
+                return fail(g, VL_EINVAL, "window size must be within 1..n per dimension");
+    Window Wn = make_window(G, origin, size);
+    Scratch sc(g);
+    const int64_t chunk = 4096;
+    int64_t nchunk = (Wn.ncell + chunk - 1) / chunk;
+    uint32_t* ccnt = (uint32_t*)sc.get((size_t)nchunk * chunk * 4);
+    uint32_t* cexc = (uint32_t*)sc.get((size_t)nchunk * chunk * 4);
+    uint32_t* ctot = (uint32_t*)sc.get((size_t)nchunk * 4);
+    int64_t* cbase = (int64_t*)sc.get(((size_t)nchunk + 1) * 8);
+    if (!ccnt || !cexc || !ctot || !cbase) return fail(g, VL_ENOMEM, "block listing: scratch allocation failed");
+    cudaMemsetAsync(ccnt, 0, (size_t)nchunk * chunk * 4, s);
+    k_cell_counts<<<nblk(Wn.ncell, 256), 256, 0, s>>>(G, Wn, L.kbits, ccnt); note_launch();
+    launch_seg_scan(ccnt, cexc, ctot, chunk, nchunk, s);
+    launch_base_scan(ctot, cbase, nchunk, s);
+    cudaMemcpyAsync(g->host_scalar, cbase + nchunk, 8, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "block listing");
+    const int64_t M = g->host_scalar[0];
+    if (count) *count = M;
+    if (!off_out) return VL_OK;
+    if (capacity < M)
+        return fail(g, VL_ECAPACITY, "vl_get_blocks: capacity " + std::to_string(capacity) +
+                                         " < " + std::to_string(M) + " blocks");
+    if (M > 0 && (!ids_out || !vals_out)) return fail(g, VL_EINVAL, "vl_get_blocks: null pointer");
+    int64_t* rank_of = (int64_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 8);
+    int64_t* d_off = on_device ? off_out : (int64_t*)sc.get((size_t)(Wn.ncell + 1) * 8);
+    uint16_t* d_ids = on_device ? ids_out : (uint16_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 2);
+    float* d_vals = on_device ? vals_out : (float*)sc.get((size_t)std::max<int64_t>(M, 1) * 256);
+    if (!rank_of || !d_off || !d_ids || !d_vals) return fail(g, VL_ENOMEM, "vl_get_blocks: scratch allocation failed");
+    k_offsets64<<<nblk(Wn.ncell + 1, 256), 256, 0, s>>>(cexc, cbase, chunk, Wn.ncell, d_off); note_launch();
+    k_fill_ids<<<nblk(Wn.ncell, 128), 128, 0, s>>>(G, Wn, L.view(), d_off, d_ids, rank_of); note_launch();
+    if (M > 0) { k_gather<<<nblk(M * 64, 256), 256, 0, s>>>(L.view(), d_ids, rank_of, d_vals, M); note_launch(); }
+    if (!on_device) {
+        cudaMemcpyAsync(off_out, d_off, (size_t)(Wn.ncell + 1) * 8, cudaMemcpyDeviceToHost, s);
+        if (M > 0) {
+            cudaMemcpyAsync(ids_out, d_ids, (size_t)M * 2, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(vals_out, d_vals, (size_t)M * 256, cudaMemcpyDeviceToHost, s);
+        }
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_get_blocks");
+    return VL_OK;
+}
+
+vl_status get_block_count(Grid* g, int64_t* n)
+{
+    return get_window(g, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0, n);
+}
+
+vl_status get_blocks(Grid* g, int64_t capacity, int64_t* off_out, uint16_t* ids_out,
+                     float* vals_out, int on_device)
+{
+    if (!off_out || capacity < 0) return fail(g, VL_EINVAL, "vl_get_blocks: null pointer");
+    return get_window(g, nullptr, nullptr, capacity, off_out, ids_out, vals_out, on_device, nullptr);
+}
+
+vl_status moments(Grid* g, double* out, int on_device)
+{
+    const GridGeom& G = g->geom;
+    const Layout& L = g->lay[g->cur];
+    if (!out) return fail(g, VL_EINVAL, "vl_moments: null pointer");
+    Scratch sc(g);
+    double* d_out = on_device ? out : (double*)sc.get((size_t)G.N * 7 * 8);
+    if (!d_out) return fail(g, VL_ENOMEM, "vl_moments: scratch allocation failed");
+    VMesh V;
+    for (int d = 0; d < 3; d++) {
+        V.vmin[d] = g->vmesh.vmin[d];
+        V.dv[d] = g->vmesh.dv[d];
+    }
+    k_moments<<<nblk(G.N * 32, 256), 256, 0, g->stream>>>(G, L.view(), V, d_out); note_launch();
+    if (!on_device)
+        cudaMemcpyAsync(out, d_out, (size_t)G.N * 7 * 8, cudaMemcpyDeviceToHost, g->stream);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_moments");
+    return VL_OK;
+}
+
+vl_status total_mass(Grid* g, double* mass)
+{
+    const GridGeom& G = g->geom;
+    Scratch sc(g);
+    double* mom = (double*)sc.get((size_t)G.N * 7 * 8);
+    double* acc = (double*)sc.get(8);
+    if (!mom || !acc) return fail(g, VL_ENOMEM, "vl_mass: scratch allocation failed");
+    vl_status st = moments(g, mom, 1);
+    if (st != VL_OK) return st;
+    cudaMemsetAsync(acc, 0, 8, g->stream);
+    k_sum_density<<<152 * 4, 256, 0, g->stream>>>(mom, G.N, acc); note_launch();
+    double h = 0.0;
+    cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, g->stream);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_mass");
+    *mass = h * g->space.dx[0] * g->space.dx[1] * g->space.dx[2];
+    return VL_OK;
+}
+
+}  // namespace vlgt

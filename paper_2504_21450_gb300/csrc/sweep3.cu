@@ -1,0 +1,205 @@
+// sweep3.cu -- the classical ("3-pass") translation of libvlgt: one kernel launch per
+// Cartesian direction, each reading and writing the whole phase space once (the
+// single-GPU analogue of the paper's per-direction ghost update, advection and remote
+// contribution, Section 2.1 / Fig. 1).
+//
+// Pass 1 reads the current layout (present blocks only) and writes every slot of the
+// next layout (the 27-cell union); passes 2 and 3 update the next layout in place.  One
+// thread walks one periodic pencil for one velocity cell with the sliding-window PPM
+// remap; the 64 threads of a block id cover its 64 velocity cells, so every step of a
+// walk is a coalesced load of 2 x 64 bytes per warp.  The last pass also raises the
+// per-chunk keep flags of the sparsity rule and sums the mass.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grid.h"
+
+namespace vlgt {
+
+namespace {
+
+constexpr int kPencils = 4;                 // pencils per CTA
+constexpr int kThreads3 = kPencils * 64;    // one thread per (pencil, velocity cell)
+constexpr int kMaxLine = 1024;              // longest pencil held in shared memory
+
+struct PassArgs {
+    GridGeom G;
+    LayoutView in, out;
+    int dim;            // physical axis of this pass
+    int check_keep_in;  // 1: read only present blocks of `in`
+    double cs;          // dt / dx_dim
+    double vmin, dv;    // velocity mesh along dim
+    int last;           // last pass: keep flags and mass
+    float thr;
+    uint8_t* keepq;
+    StepCounters* ctr;
+    int64_t groups;     // pencil groups per block id
+};
+
+// physical coordinates of pencil p, position i along dim
+__device__ __forceinline__ void pencil_cell(const GridGeom& G, int dim, int64_t p, int i, int& x,
+                                            int64_t& row)
+{
+    if (dim == 0) {
+        x = i;
+        row = p;  // row = y + ny*z
+    } else if (dim == 1) {
+        x = (int)(p % G.n[0]);
+        int64_t z = p / G.n[0];
+        row = i + (int64_t)G.n[1] * z;
+    } else {
+        x = (int)(p % G.n[0]);
+        int64_t y = p / G.n[0];
+        row = y + (int64_t)G.n[1] * i;
+    }
+}
+
+template <bool kLim>
+__global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
+{
+    __shared__ int s_rin[kPencils][kMaxLine];
+    __shared__ int s_rout[kPencils][kMaxLine];
+    __shared__ int s_any[kPencils];
+    const GridGeom& G = P.G;
+    const int b = (int)(blockIdx.x / P.groups);
+    const int64_t grp = blockIdx.x % P.groups;
+    const int nd = G.n[P.dim];
+    const int64_t npen = G.N / nd;
+    if (P.out.cnt[b] == 0) return;
+
+    // ranks of every cell of the CTA's pencils in both layouts
+    if (threadIdx.x < kPencils) s_any[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kPencils * nd; t += blockDim.x) {
+        int k = t / nd, i = t - k * nd;
+        int64_t p = grp * kPencils + k;
+        int ri = -1, ro = -1;
+        if (p < npen) {
+            int x;
+            int64_t row;
+            pencil_cell(G, P.dim, p, i, x, row);
+            ri = (int)cell_rank(P.in, G, b, x, row, P.check_keep_in != 0);
+            ro = (int)cell_rank(P.out, G, b, x, row, false);
+        }
+        s_rin[k][i] = ri;
+        s_rout[k][i] = ro;
+        if (ro >= 0) s_any[k] = 1;
+    }
+    __syncthreads();
+    const int k = threadIdx.x >> 6;
+    const int v = threadIdx.x & 63;
+    if (!s_any[k]) return;  // nothing of this pencil is in the next layout (warp-uniform)
+
+    const int q = v >> 4, l = v & 15;
+    int bc[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
+    int within[3] = {v & 3, (v >> 2) & 3, v >> 4};
+    int iv = bc[P.dim] * 4 + within[P.dim];
+    const SweepConst kc = sweep_const((P.vmin + (iv + 0.5) * P.dv) * P.cs);
+
+    const float* src = P.in.pool + ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + l;
+    float* dst = P.out.pool + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + l;
+    const int* rin = s_rin[k];
+    const int* rout = s_rout[k];
+    auto load = [&](int w) -> float {
+        int r = rin[w];
+        return r >= 0 ? src[(int64_t)r * kChunk] : 0.0f;
+    };
+    // originals of the cells that the wrapped tail reads again after they were written
+    const float t0 = load(0), t1 = load(1 % nd), t2 = load(2 % nd);
+
+    Slide<kLim> s;
+    s.reset();
+    float msum = 0.0f;
+    double mass = 0.0;
+    const float thr = P.thr;
+    auto emit = [&](int kk, float res) {
+        int r = rout[kk];
+        if (r >= 0) dst[(int64_t)r * kChunk] = res;
+        if (P.last) {
+            bool keep = r >= 0 && res >= thr;
+            unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (r >= 0 && (threadIdx.x & 15) == 0) {
+                unsigned half = (threadIdx.x & 16) ? (m >> 16) : (m & 0xffffu);
+                P.keepq[((int64_t)P.out.base[b] + r) * 4 + q] = half ? 1 : 0;
+            }
+            if (r >= 0) msum += res;
+        }
+    };
+    int i = -3;
+    for (; i < 0; i++) s.push(load(wrapi(i, nd)), kc);
+    // main walk, loads batched ahead of the dependent arithmetic
+    for (; i + 8 <= nd; i += 8) {
+        float a[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) a[u] = load(i + u);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            float res = s.push(a[u], kc);
+            if (i + u >= 3) emit(i + u - 3, res);
+        }
+        if (P.last) {
+            mass += (double)msum;
+            msum = 0.0f;
+        }
+    }
+    for (; i < nd; i++) {
+        float res = s.push(load(i), kc);
+        if (i >= 3) emit(i - 3, res);
+    }
+    const float tail[3] = {t0, t1, t2};
+#pragma unroll
+    for (int u = 0; u < 3; u++, i++) {
+        float res = s.push(tail[u], kc);
+        if (i >= 3) emit(i - 3, res);
+    }
+    if (P.last) {
+        mass += (double)msum;
+        for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
+        if ((threadIdx.x & 31) == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
+    }
+}
+
+}  // namespace
+
+vl_status run_3pass(Grid* g, const StepArgs& a)
+{
+    const GridGeom& G = g->geom;
+    Layout& A = g->lay[g->cur];
+    Layout& B = g->lay[1 - g->cur];
+    for (int d = 0; d < 3; d++)
+        if (G.n[d] > kMaxLine)
+            return fail(g, VL_EINVAL, "3-pass form: grid extent above 1024 cells");
+    cudaEventRecord(g->ev_sweep0, g->stream);
+    for (int j = 0; j < 3; j++) {
+        int d = a.order[j];
+        PassArgs P;
+        P.G = G;
+        P.in = j == 0 ? A.view() : B.view();
+        P.out = B.view();
+        P.dim = d;
+        P.check_keep_in = j == 0 ? 1 : 0;
+        P.cs = a.c_scale[d];
+        P.vmin = g->vmesh.vmin[d];
+        P.dv = g->vmesh.dv[d];
+        P.last = j == 2 ? 1 : 0;
+        P.thr = (float)g->threshold;
+        P.keepq = B.keepq;
+        P.ctr = g->counters;
+        int64_t npen = G.N / G.n[d];
+        P.groups = (npen + kPencils - 1) / kPencils;
+        int64_t nblocks = P.groups * G.nb;
+        if (nblocks > 0x7fffffffLL) return fail(g, VL_EINVAL, "3-pass form: grid too large");
+        if (a.limiter) {
+            k_pass<true><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P); note_launch();
+        }
+        else {
+            k_pass<false><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P); note_launch();
+        }
+    }
+    cudaEventRecord(g->ev_sweep1, g->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(g, e, "3-pass sweep launch");
+    return VL_OK;
+}
+
+}  // namespace vlgt

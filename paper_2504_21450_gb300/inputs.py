@@ -251,3 +251,37 @@ def random_blocks(n, nv, density: float, seed: int, scale: float = 1.0,
     if not positive:
         v = 2.0 * v - 1.0
     return Initial(tuple(n), off, bi.astype(np.uint16), (scale * v).astype(np.float32), 0.0)
+
+
+def generate_torch(cfg: Config, device, origin=(0, 0, 0), size=None, thr: float | None = None,
+                   chunk: int = 2048):
+    """The same initial state as ``generate`` built on a CUDA device with torch (for
+    workloads too large for host memory).  The FP64 sum over populations is evaluated in
+    the same elementwise order as on the host, so the float32 values agree bit for bit.
+    Returns (off, ids, vals, threshold) as CUDA tensors (int64, int32, float32 [M,64])."""
+    import torch
+    size = tuple(cfg.n if size is None else size)
+    thr = threshold(cfg) if thr is None else thr
+    G = torch.from_numpy(population_tables(cfg)).to(device)
+    cells = window_cells(cfg, origin, size)
+    counts = torch.zeros(cells.size, dtype=torch.int64, device=device)
+    parts_ids, parts_vals = [], []
+    for s in range(0, cells.size, chunk):
+        cc = cells[s:s + chunk]
+        w = torch.from_numpy(cell_weights(cfg, cc)).to(device)
+        f = w[:, 0, None, None] * G[0][None]
+        for k in range(1, len(cfg.pops)):
+            f = f + w[:, k, None, None] * G[k][None]
+        f32 = f.to(torch.float32)
+        del f
+        keep = f32.amax(dim=2).to(torch.float64) >= thr
+        counts[s:s + cc.size] = keep.sum(dim=1)
+        ci, bi = torch.nonzero(keep, as_tuple=True)
+        parts_ids.append(bi.to(torch.int32))
+        parts_vals.append(f32[ci, bi])
+        del f32, keep
+    off = torch.zeros(cells.size + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=off[1:])
+    ids = torch.cat(parts_ids) if parts_ids else torch.zeros(0, dtype=torch.int32, device=device)
+    vals = torch.cat(parts_vals) if parts_vals else torch.zeros((0, 64), dtype=torch.float32, device=device)
+    return off, ids, vals, thr

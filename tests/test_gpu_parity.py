@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs -- fused (Ghost Translation) and 3-pass (classical) forms."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_21450_gb300 import inputs, vlasov
+
+from parity import GUARD, MASS_TOL, VAL_TOL, compare_step, gpu_grid
+
+pytestmark = pytest.mark.gpu
+
+FORMS = {"fused": vlasov.VL_FORM_FUSED, "3pass": vlasov.VL_FORM_3PASS}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    vlasov.load(build_if_missing=True)
+    oracle.build()
+
+
+def as_ref(init):
+    return oracle.as_blocks(init.off, init.ids, init.vals.astype(np.float64))
+
+
+def mesh_of(cfg, n=None):
+    return oracle.Mesh(n=tuple(n or cfg.n), nv=cfg.nv, vmin=cfg.vmin, dv=cfg.dv, dx=cfg.dx)
+
+
+@pytest.mark.parametrize("form", ["fused", "3pass"])
+def test_tiny_config_matches_oracle(form):
+    cfg = inputs.CONFIGS["tiny"]
+    init = inputs.generate(cfg)
+    mesh = mesh_of(cfg)
+    g = gpu_grid(mesh, init.threshold)
+    g.set_blocks(init.off, init.ids, init.vals)
+    m0 = g.mass()
+    g.translate(cfg.dt, "xyz", 1, FORMS[form], check=True)
+    after = g.get_blocks()
+    err, fmax, amb, ref, st = compare_step(mesh, as_ref(init), after, init.threshold, cfg.dt)
+    assert amb == 0
+    assert err <= VAL_TOL * fmax, (err, fmax)
+    m_ref = oracle.mass(mesh, ref)
+    assert abs(g.mass() - m_ref) <= MASS_TOL * m_ref
+    assert abs(g.stats().mass - m_ref) <= MASS_TOL * m_ref
+    assert abs(m0 - oracle.mass(mesh, as_ref(init))) <= 1e-12 * m_ref
+
+
+def run_forms(mesh, init, dt, order, steps, limiter=True):
+    out = {}
+    for name, form in FORMS.items():
+        g = gpu_grid(mesh, init.threshold)
+        g.set_blocks(init.off, init.ids, init.vals)
+        g.translate(dt, order, steps, form, limiter=limiter, check=True)
+        out[name] = g.get_blocks()
+        g.close()
+    return out
+
+
+@pytest.mark.parametrize("order", ["xyz", "zxy", "yzx"])
+def test_fused_equals_3pass_bit_for_bit(order):
+    """Ghost Translation computes the same floating-point operations per cell as the
+    classical form (Section 3: the result is correct data in the local domain)."""
+    init = inputs.random_blocks((37, 19, 11), (8, 8, 8), 0.3, seed=40)
+    mesh = oracle.Mesh(n=(37, 19, 11), nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    init.threshold = 0.05
+    out = run_forms(mesh, init, 0.2, order, 2)
+    for a, b in zip(out["fused"], out["3pass"]):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("form", ["fused", "3pass"])
+@pytest.mark.parametrize("order", ["xyz", "zxy"])
+def test_sparse_ragged_tiles_step_by_step(form, order):
+    """Several tiles with ragged tails, sparse blocks, pruning: each GPU step is checked
+    against one oracle step started from the GPU's own previous state."""
+    n = (37, 19, 11)
+    init = inputs.random_blocks(n, (8, 8, 12), 0.25, seed=41)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 12), vmin=(-4.0, -4.0, -6.0), dv=(1.0,) * 3, dx=(1.0, 1.0, 1.5))
+    thr = 0.3
+    g = gpu_grid(mesh, thr)
+    g.set_blocks(init.off, init.ids, init.vals)
+    before = as_ref(init)
+    for step in range(3):
+        g.translate(0.15, order, 1, FORMS[form], check=True)
+        after = g.get_blocks()
+        err, fmax, amb, ref, st = compare_step(mesh, before, after, thr, 0.15, order)
+        assert err <= VAL_TOL * fmax, (step, err, fmax)
+        assert st.kept_blocks < st.union_blocks  # the sparsity rule removed blocks
+        s = g.stats()
+        assert abs(s.dropped_mass - st.dropped_mass) <= 1e-5 * max(st.dropped_mass, 1e-30)
+        before = oracle.as_blocks(*[np.asarray(a) for a in after[:2]], after[2].astype(np.float64))
+
+
+def test_limiter_off_dense():
+    n = (20, 9, 7)
+    init = inputs.random_blocks(n, (8, 4, 4), 1.0, seed=42, positive=False)
+    mesh = oracle.Mesh(n=n, nv=(8, 4, 4), vmin=(-4.0, -2.0, -2.0), dv=(1.0,) * 3)
+    for name, form in FORMS.items():
+        g = gpu_grid(mesh, 0.0)
+        g.set_blocks(init.off, init.ids, init.vals)
+        g.translate(0.2, "yxz", 1, form, limiter=False, check=True)
+        ref, _ = oracle.translate(mesh, as_ref(init), 0.2, "yxz", limiter=False)
+        off, ids, vals = g.get_blocks()
+        np.testing.assert_array_equal(off, ref.off)
+        assert np.abs(vals - ref.vals).max() <= VAL_TOL * np.abs(ref.vals).max()
+
+
+def test_whole_cell_shift_at_unit_courant():
+    n = (6, 5, 4)
+    mesh = oracle.Mesh(n=n, nv=(4, 4, 4), vmin=(-2.0,) * 3, dv=(1.0,) * 3, dx=(1.5,) * 3)
+    rng = np.random.default_rng(43)
+    ncell = int(np.prod(n))
+    vals = rng.uniform(0.1, 1.0, (ncell, 64)).astype(np.float32)
+    for form in FORMS.values():
+        g = gpu_grid(mesh, 0.0)
+        g.set_blocks(np.arange(ncell + 1), np.zeros(ncell, np.uint16), vals)
+        g.translate(1.0, "zxy", 1, form, check=True)
+        _, _, out = g.get_blocks()
+        for v in (0, 3, 12, 15, 48, 51, 60, 63):
+            iv = (v % 4, (v // 4) % 4, v // 16)
+            s = [1 if i == 3 else -1 for i in iv]
+            want = np.roll(vals[:, v].reshape(n[2], n[1], n[0]), (s[2], s[1], s[0]), axis=(0, 1, 2))
+            np.testing.assert_allclose(out[:, v].reshape(n[2], n[1], n[0]), want, rtol=3e-7)
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (1, 2, 3), (3, 1, 70), (65, 2, 1), (130, 3, 2)])
+def test_degenerate_and_wide_grids(n):
+    init = inputs.random_blocks(n, (8, 8, 8), 0.5, seed=44)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    for form in FORMS.values():
+        g = gpu_grid(mesh, 0.1)
+        g.set_blocks(init.off, init.ids, init.vals)
+        g.translate(0.2, "xzy", 1, form, check=True)
+        err, fmax, amb, _, _ = compare_step(mesh, as_ref(init), g.get_blocks(), 0.1, 0.2, "xzy")
+        assert err <= VAL_TOL * fmax
+
+
+def test_empty_state_and_errors():
+    mesh = oracle.Mesh(n=(4, 4, 4), nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    g = gpu_grid(mesh, 0.0)
+    with pytest.raises(vlasov.VlError) as e:
+        g.translate(0.1)
+    assert e.value.status == vlasov.VL_ESTATE
+    g.set_blocks(np.zeros(65, np.int64), np.zeros(0, np.uint16), np.zeros((0, 64), np.float32))
+    g.translate(0.1, "xyz", 2, check=True)
+    assert g.block_count() == 0
+    with pytest.raises(vlasov.VlError) as e:
+        g.translate(0.3)  # |v| = 3.5 -> c = 1.05
+    assert e.value.status == vlasov.VL_ECFL
+    with pytest.raises(vlasov.VlError) as e:
+        g.translate(0.1, "xxy")
+    assert e.value.status == vlasov.VL_EINVAL
+    off = np.zeros(65, np.int64)
+    off[1:] = 2
+    with pytest.raises(vlasov.VlError) as e:
+        g.set_blocks(off, np.array([3, 1], np.uint16), np.zeros((2, 64), np.float32))
+    assert e.value.status == vlasov.VL_EINVAL
+    with pytest.raises(vlasov.VlError) as e:
+        g.set_blocks(off, np.array([1, 99], np.uint16), np.zeros((2, 64), np.float32))
+    assert e.value.status == vlasov.VL_EINVAL
+
+
+def test_mass_conservation_and_moments():
+    n = (12, 10, 8)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.6, seed=45)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(0.5, 1.0, 1.0), dx=(1.0, 2.0, 1.0))
+    g = gpu_grid(mesh, 0.0)
+    g.set_blocks(init.off, init.ids, init.vals)
+    m0 = g.mass()
+    np.testing.assert_allclose(g.moments(), oracle.moments(mesh, as_ref(init)), rtol=1e-11, atol=1e-13)
+    g.translate(0.1, "xyz", 5, check=True)
+    assert abs(g.mass() - m0) <= MASS_TOL * m0
+    s = g.stats()
+    assert s.steps == 5 and s.dropped_blocks == 0 and abs(s.mass - m0) <= MASS_TOL * m0
+
+
+@pytest.mark.parametrize("form", ["fused", "3pass"])
+def test_uniform_config_full_size_window(form):
+    """The 64^3 x 32^3 workload at full size, in the configuration the benchmark times:
+    a 16^3 window of the state is read before and after one step, and the oracle
+    recomputes the 10^3 interior (dependence radius 3 per step) from the window."""
+    import torch
+    cfg = inputs.CONFIGS["uniform"]
+    off, ids, vals, thr = inputs.generate_torch(cfg, "cuda")
+    mesh = mesh_of(cfg)
+    g = gpu_grid(mesh, thr)
+    g.set_blocks(off, ids, vals)
+    del off, ids, vals
+    torch.cuda.empty_cache()
+    origin, size = (55, 7, 60), (16, 16, 16)  # wraps around x and z
+    pre = g.get_window(origin, size)
+    g.translate(cfg.dt, "xyz", 1, FORMS[form], check=True)
+    post = g.get_window(origin, size)
+    wmesh = oracle.Mesh(n=size, nv=cfg.nv, vmin=cfg.vmin, dv=cfg.dv, dx=cfg.dx, periodic=False)
+    inner = [x + size[0] * (y + size[1] * z) for z in range(3, 13) for y in range(3, 13) for x in range(3, 13)]
+    err, fmax, amb, _, _ = compare_step(wmesh, oracle.as_blocks(pre[0], pre[1], pre[2].astype(np.float64)),
+                                        post, thr, cfg.dt, "xyz", cells=inner)
+    assert err <= VAL_TOL * fmax, (err, fmax)
+    g.close()
