@@ -326,10 +326,15 @@ def main():
     ap.add_argument("--form", default="fused", choices=["fused", "3pass"])
     ap.add_argument("--config", default="uniform", choices=sorted(inputs.CONFIGS))
     ap.add_argument("--order", default="xyz")
+    ap.add_argument("--grid", type=int, nargs=3, default=None,
+                    help="override the spatial extent (smaller cases for profiling)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     cfg = inputs.CONFIGS[args.config]
+    if args.grid:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, n=tuple(args.grid), name=f"{cfg.name}-{'x'.join(map(str, args.grid))}")
     if args.impl == "reference":
         run_reference(args, cfg)
     else:

@@ -186,9 +186,15 @@ vl_status vl_grid_create(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
         g->item_base = (int64_t*)g->alloc(((size_t)nb + 1) * 8);
         if (!g->counters || !g->item_cnt || !g->item_base) st = fail(g, VL_ENOMEM, "vl_grid_create: allocation failed");
     }
+    const int nvmax = std::max(vmesh->nv[0], std::max(vmesh->nv[1], vmesh->nv[2]));
+    if (st == VL_OK) {
+        g->ctab = (float4*)g->alloc((size_t)6 * nvmax * sizeof(float4));
+        if (!g->ctab) st = fail(g, VL_ENOMEM, "vl_grid_create: allocation failed");
+    }
     if (st == VL_OK) {
         cudaError_t e = cudaMallocHost((void**)&g->counters_host, sizeof(StepCounters));
         if (e == cudaSuccess) e = cudaMallocHost((void**)&g->host_scalar, 64);
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&g->ctab_host, (size_t)6 * nvmax * sizeof(float4));
         if (e != cudaSuccess) st = cuda_fail(g, e, "vl_grid_create: pinned host memory");
     }
     if (st == VL_OK) {
@@ -221,6 +227,8 @@ vl_status vl_grid_destroy(vl_grid* grid)
     g->release(g->item_mass);
     if (g->ev_sweep0) cudaEventDestroy(g->ev_sweep0);
     if (g->ev_sweep1) cudaEventDestroy(g->ev_sweep1);
+    g->release(g->ctab);
+    if (g->ctab_host) cudaFreeHost(g->ctab_host);
     if (g->counters_host) cudaFreeHost(g->counters_host);
     if (g->host_scalar) cudaFreeHost(g->host_scalar);
     delete g;
@@ -326,6 +334,28 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
             return fail(g, VL_ECFL, "vl_translate: max |v_d| dt / dx_d = " + std::to_string(c) + " > 1");
         a.c_scale[d] = dt / g->space.dx[d];
     }
+    // per-velocity-cell sweep constants (Courant number c = v_d dt / dx_d at the cell
+    // centre, Section 2.1), computed in FP64 once per dt and rounded to FP32
+    const int nvmax = std::max(g->vmesh.nv[0], std::max(g->vmesh.nv[1], g->vmesh.nv[2]));
+    if (g->ctab_dt != dt) {
+        cudaStreamSynchronize(g->stream);
+        for (int d = 0; d < 3; d++)
+            for (int i = 0; i < nvmax; i++) {
+                double c = i < g->vmesh.nv[d]
+                               ? (g->vmesh.vmin[d] + (i + 0.5) * g->vmesh.dv[d]) * dt / g->space.dx[d]
+                               : 0.0;
+                WalkConst w = walk_const(c);
+                SweepConst k = sweep_const(c);
+                g->ctab_host[d * nvmax + i] = make_float4(w.g, w.A, w.B, (float)w.up);
+                g->ctab_host[3 * nvmax + d * nvmax + i] = make_float4(k.g, k.A, k.B, (float)k.up);
+            }
+        cudaMemcpyAsync(g->ctab, g->ctab_host, (size_t)6 * nvmax * sizeof(float4), cudaMemcpyHostToDevice,
+                        g->stream);
+        g->ctab_dt = dt;
+    }
+    a.walk = g->ctab;
+    a.sweep = g->ctab + 3 * nvmax;
+    a.nvmax = nvmax;
     a.limiter = opts.limiter ? 1 : 0;
     a.tile[0] = opts.tile[0];
     a.tile[1] = opts.tile[1];
@@ -356,6 +386,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
         if (st != VL_OK) break;
         st = layout_ensure_pool(g, B, std::max<int64_t>(total, 1));
         if (st != VL_OK) break;
+        cudaMemsetAsync(B.keepq, 0, (size_t)std::max<int64_t>(total, 1) * 4, g->stream);
         st = fused ? run_fused(g, a) : run_3pass(g, a);
         if (st != VL_OK) break;
         cudaEventRecord(ep, g->stream);
@@ -379,7 +410,9 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
         prune_ms += ms;
         const StepCounters& C = *g->counters_host;
         if (C.error) {
-            st = fail(g, VL_ECUDA, "vl_translate: device-side error flag " + std::to_string(C.error));
+            st = fail(g, (C.error & 4) ? VL_ETIMEOUT : VL_ECUDA,
+                      "vl_translate: device-side error flag " + std::to_string(C.error) +
+                          ((C.error & 4) ? " (a staging barrier wait ran out)" : ""));
             break;
         }
         S.steps++;

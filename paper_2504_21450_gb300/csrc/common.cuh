@@ -133,6 +133,81 @@ struct Slide {
     }
 };
 
+// min(|a|, |b|) carrying the sign sign(a) XOR sign(b): positive when a and b agree in
+// sign, so max(result, 0) is the magnitude of minmod(a, b).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b)
+{
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Per-velocity-cell constants of a sweep walked in the upwind-to-downwind direction:
+// in that frame c >= 0 always (a cell with c < 0 is the mirror image of one with
+// c > 0), g = |c|, A = g (1-g)^2, B = g^2 (1-g).
+struct WalkConst {
+    float g, A, B;
+    int up;  // 1: walk towards higher indices (c >= 0); 0: walk towards lower ones
+};
+
+__host__ __device__ inline WalkConst walk_const(double c)
+{
+    WalkConst k;
+    double g = c >= 0.0 ? c : -c;
+    k.g = (float)g;
+    k.A = (float)(g * (1.0 - g) * (1.0 - g));
+    k.B = (float)(g * g * (1.0 - g));
+    k.up = c >= 0.0 ? 1 : 0;
+    return k;
+}
+
+// PPM remap of one line walked from upwind to downwind, one cell average pushed per
+// call; after the value of cell p (walking order) is pushed, the new average of cell
+// p-2 is returned (inflow from the upwind neighbour p-3, outflow towards p-1).  Same
+// reading of the paper as Slide, evaluated with the edge distances kept signed:
+//   d1 = e clamped into [0, delta]  as  copysign(max(minxs(e, delta), 0), delta)
+//   out = g a + sign(d1) max(A u + B w, 0),  u = minxs(d1, 2 d0), w = minxs(d0, 2 d1)
+// where minxs = min_xorsign_abs.  When d0 and d1 differ in sign (a local extremum) u
+// and w are <= 0 and the cell sends g a, as CW84's flattening prescribes; otherwise
+// |u| = |minmod(d1, 2 d0)| and |w| = |minmod(d0, 2 d1)|.
+template <bool kLimiter>
+struct Walk {
+    float a1, a2;  // a_{p-1}, a_{p-2}
+    float l1, l2;  // delta_{p-2}, delta_{p-3}
+    float d0;      // d0_{p-2}
+    float o3;      // out_{p-3}
+
+    __device__ __forceinline__ void reset()
+    {
+        a1 = a2 = l1 = l2 = d0 = o3 = 0.0f;
+    }
+
+    __device__ __forceinline__ float push(float a, const WalkConst& k)
+    {
+        float dn = a - a1;                                          // delta_{p-1}
+        float e = fmaf(l2 - dn, 1.0f / 12.0f, 0.5f * l1);           // e_{p-2}
+        float d1, out;
+        if (kLimiter) {
+            d1 = copysignf(fmaxf(min_xorsign_abs(e, l1), 0.0f), l1);
+            float u = min_xorsign_abs(d1, d0 + d0);
+            float w = min_xorsign_abs(d0, d1 + d1);
+            float xm = fmaxf(fmaf(k.A, u, k.B * w), 0.0f);
+            out = fmaf(k.g, a2, copysignf(xm, d1));                 // out_{p-2}
+        } else {
+            d1 = e;
+            out = fmaf(k.B, d0, fmaf(k.A, d1, k.g * a2));
+        }
+        float res = (a2 - out) + o3;                                // new a_{p-2}
+        d0 = l1 - d1;                                               // d0_{p-1}
+        a2 = a1;
+        a1 = a;
+        l2 = l1;
+        l1 = dn;
+        o3 = out;
+        return res;
+    }
+};
+
 // Slot (rank) of cell (x, row) of block id b in a layout, or -1 when the cell has no
 // slot.  With check_keep the cell must also hold the block (kbits).
 __device__ __forceinline__ int64_t cell_rank(const LayoutView& L, const GridGeom& G, int b,

@@ -2,20 +2,29 @@
 // one kernel over a spatial tile plus its ghost halo (paper Section 3).
 //
 // A work item is (block id b, velocity chunk q, tile column).  The tile spans TX x TY
-// cells along the first two sweep axes and the whole periodic extent of the third axis,
-// which is streamed plane by plane.  Every plane of the tile plus a halo of 3 cells
-// (GT3: the 2-cell stencil plus one face neighbour, Section 3.1) is staged into shared
-// memory exactly once with 16-byte cp.async copies (the coalesced ghost update); the
-// first sweep then runs on the tile rows widened by the halo along the second axis
-// (the paper's active cells of the first sweep), the second sweep on the tile, and the
-// third sweep consumes the planes from a 7-deep sliding window that each thread keeps
-// in registers, so that no intermediate result goes back to HBM.
+// cells along the first two sweep axes and the whole periodic extent of the third
+// axis, which is streamed plane by plane.  Every plane of the tile plus a halo of 3
+// cells (GT3: the 2-cell stencil plus one face neighbour, Section 3.1) is staged into
+// shared memory exactly once with 16-byte cp.async copies (the single coalesced ghost
+// update).  Sweep 0 then runs on all halo rows (the active cells of the first sweep),
+// sweep 1 on the tile columns, and sweep 2 consumes the planes through a sliding
+// window that each thread keeps in registers, so no intermediate result goes to HBM.
 //
-// Thread layout (256 threads): lane v = tid % 16 is the velocity cell of the chunk;
-// first sweep: tid / 16 = halo row (14 rows); second and third sweeps: tid / 16 = tile
-// column along axis 0, each thread owning the TY cells of that column.
+// Each sweep walks its line from the upwind side (Walk), so its arithmetic has no
+// sign-dependent selects.  When the streamed axis is the velocity chunk's own axis
+// (sweep order ending in z, the chunk being a vz plane), every velocity cell of an
+// item shares the sign of c along it and the planes are streamed upwind-first too;
+// otherwise the streamed sweep uses the sign-generic window (Slide).
+//
+// Thread roles (512 threads, lane = velocity cell): during sweep 0 the threads of the
+// halo rows (22 x 16) run it while the others stage the next planes, compute output
+// slots of sparse layouts and write the per-chunk keep flags of the sparsity rule;
+// then every thread runs sweep 1 on one segment of a tile column (TY/2 rows) and keeps
+// the streamed windows of those cells for sweep 2.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "grid.h"
 
@@ -23,26 +32,39 @@ namespace vlgt {
 
 namespace {
 
-constexpr int TX = 16, TY = 8;
-constexpr int NT = 256;
-constexpr int NST = 3;                     // pipeline stages of staged planes
-constexpr int EX = TX + 2 * kHalo;         // 22
-constexpr int EY = TY + 2 * kHalo;         // 14
-constexpr int SROW = EX * kChunk + 16;     // padded stage row (floats); 16 mod 32 keeps
-constexpr int STAGE = EY * SROW;           // two rows of a warp on distinct banks
-constexpr int XROW = TX * kChunk + 16;
-constexpr int XBUF = EY * XROW;
-constexpr int kSmemBytes = (NST * STAGE + XBUF) * 4 + 2 * TX * TY * 4 + 64;
+constexpr int NV = kChunk;   // velocity cells per item (one vz plane of a block)
+constexpr int H = kHalo;
+constexpr int TX = 16;
+constexpr int NT = 512;
+constexpr int NST = 3;               // pipeline stages of staged planes
+constexpr int EX = TX + 2 * H;       // 22 halo columns
+constexpr int SROW = EX * NV + 16;   // padded stage row (floats), 16 mod 32
+constexpr int XROW = TX * NV + 16;   // padded sweep-0 output row
 
-static_assert(EY * kChunk <= NT, "first-sweep rows must fit the CTA");
-static_assert(TX * kChunk == NT, "second-sweep columns must match the CTA");
+template <int TY_>
+struct Shape {
+    static constexpr int TY = TY_;
+    static constexpr int EY = TY + 2 * H;
+    static constexpr int NX = EY * NV;        // threads of sweep 0
+    static constexpr int NLD = NT - NX;       // threads staging planes meanwhile
+    static constexpr int NH = NT / (TX * NV); // sweep-1 segments per tile column
+    static constexpr int L = TY / NH;         // tile rows per sweep-1 segment
+    static constexpr int STAGE = EY * SROW;
+    static constexpr int XBUF = EY * XROW;
+    static constexpr int TABS = 2 * EX + 2 * EY;
+    static constexpr int SMEM = (NST * STAGE + XBUF) * 4 + TABS * 4 + 2 * TX * TY * 4 + 2 * 16 * 4 + 64;
+    static_assert(NX < NT, "sweep-0 rows must leave threads to stage planes");
+    static_assert(NH * TX * NV == NT && NH * L == TY, "sweep-1 segments must tile the CTA");
+};
 
 struct FusedArgs {
     GridGeom G;
     LayoutView in, out;
     int ax[3];           // physical axis of sweep 0, 1, 2 (axis 2 is streamed)
-    double cs[3];        // dt / dx of sweep j's axis
-    double vmin[3], dv[3];
+    int64_t stride[3];   // cell-index stride of each physical axis (1, nx, nx*ny)
+    const float4* walk;   // [3][nvmax] WalkConst (g, A, B, up) per axis and velocity index
+    const float4* sweep;  // [3][nvmax] SweepConst (g, A, B, up)
+    int nvmax;
     float thr;
     int ntile0;          // tiles along sweep axis 0
     const uint32_t* items;
@@ -61,47 +83,103 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ void to_phys(const int ax[3], int l0, int l1, int l2, int& x, int& y, int& z)
+// x and row contributions of coordinate c along physical axis d
+__device__ __forceinline__ int xpart(int d, int c) { return d == 0 ? c : 0; }
+__device__ __forceinline__ int rpart(int d, int c, int ny) { return d == 1 ? c : (d == 2 ? c * ny : 0); }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
 {
-    int p[3];
-    p[ax[0]] = l0;
-    p[ax[1]] = l1;
-    p[ax[2]] = l2;
-    x = p[0];
-    y = p[1];
-    z = p[2];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1D bulk copy global -> shared (TMA), completion counted on an mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
-template <bool kLim>
-__global__ void __launch_bounds__(NT, 2) k_fused(FusedArgs P)
+// Upper bound on polls of a staging barrier before the kernel gives up: far beyond any
+// real copy time (a plane is a few tens of kB), so reaching it means a fault upstream.
+constexpr unsigned kMaxPolls = 1u << 24;
+
+template <int TY, bool kLim, bool kZUni>
+__global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 {
+    using S = Shape<TY>;
+    constexpr int EY = S::EY;
+    constexpr int NLD = S::NLD, L = S::L;
     extern __shared__ __align__(16) float smem[];
     float* stage = smem;
-    float* xbuf = smem + NST * STAGE;
-    int* orank = reinterpret_cast<int*>(xbuf + XBUF);  // [2][TY][TX]
+    float* xbuf = stage + NST * S::STAGE;
+    int* px0 = reinterpret_cast<int*>(xbuf + S::XBUF);
+    int* pr0 = px0 + EX;
+    int* px1 = pr0 + EX;
+    int* pr1 = px1 + EY;
+    int* orank = pr1 + EY;                                           // [2][TY][TX]
+    unsigned* kb = reinterpret_cast<unsigned*>(orank + 2 * TX * TY);  // [2][16 warps]
     __shared__ int64_t s_work;
+    __shared__ __align__(8) uint64_t s_bar[NST];  // staging barriers of the bulk copies
+    __shared__ int s_run[EX][3];                  // contiguous runs of a halo row: u0, x, len
+    __shared__ int s_nrun;
 
     const GridGeom& G = P.G;
     const int tid = threadIdx.x;
     const int v = tid & 15;
-    const int hi = tid >> 4;  // halo row (sweep 0) / tile column (sweeps 1, 2)
-    const int n0 = G.n[P.ax[0]], n1 = G.n[P.ax[1]], n2 = G.n[P.ax[2]];
+    const int hi = tid >> 4;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int a0 = P.ax[0], a1 = P.ax[1], a2 = P.ax[2];
+    const int n0 = G.n[a0], n1 = G.n[a1], n2 = G.n[a2];
+    const int ny = G.n[1];
     const int64_t nwork = 4 * P.item_base[G.nb];
-    const int nplanes = n2 + 2 * kHalo;
+    // The streamed window returns the new average of the plane 2 (Walk) or 3 (Slide)
+    // positions behind the one pushed, and the first pushed plane is 3 before the
+    // first cell: outputs start at step FIRST and cover steps FIRST .. n2+FIRST-1.
+    constexpr int FIRST = H + (kZUni ? 2 : 3);
+    const int nsteps = n2 + FIRST;  // planes streamed per item
+    const bool loader = tid >= S::NX;
+    const int ltid = tid - S::NX;
+    const int ci = hi & (TX - 1);       // sweep-1 segment: tile column ci,
+    const int j0 = (tid / (TX * NV)) * L;  // rows j0 .. j0+L-1
+
+    if (tid == 0) {
+        for (int k = 0; k < NST; k++) mbar_init(&s_bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    unsigned gstep = 0;  // planes staged by this CTA so far (barrier phases)
 
     for (;;) {
-        __syncthreads();  // previous item fully done with shared memory
+        __syncthreads();
         if (tid == 0) s_work = (int64_t)atomicAdd(&P.ctr->work_next, 1ull);
         __syncthreads();
         const int64_t w = s_work;
         if (w >= nwork) break;
 
-        // decode (b, q, tile): items are grouped by b; within b, q-major then tile
-        int lo = 0, hi_b = G.nb;
-        while (hi_b - lo > 1) {
-            int mid = (lo + hi_b) >> 1;
+        // ---- decode (b, q, tile); items are grouped by b, q-major then tile --------
+        int lo = 0, hb = G.nb;
+        while (hb - lo > 1) {
+            int mid = (lo + hb) >> 1;
             if (4 * P.item_base[mid] <= w) lo = mid;
-            else hi_b = mid;
+            else hb = mid;
         }
         const int b = lo;
         const int64_t mb = P.item_base[b + 1] - P.item_base[b];
@@ -111,117 +189,265 @@ __global__ void __launch_bounds__(NT, 2) k_fused(FusedArgs P)
         const int t0 = (int)(tile % P.ntile0) * TX;
         const int t1 = (int)(tile / P.ntile0) * TY;
         const int e0 = min(TX, n0 - t0), e1 = min(TY, n1 - t1);
-
-        // per-thread velocity cell (chunk q = vz plane of the block; v = vx + 4 vy)
-        const int bcoord[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
-        const int within[3] = {v & 3, v >> 2, q};
-        SweepConst kc[3];
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            int d = P.ax[j];
-            int iv = bcoord[d] * 4 + within[d];
-            kc[j] = sweep_const((P.vmin[d] + (iv + 0.5) * P.dv[d]) * P.cs[j]);
-        }
-        const int64_t ibase = ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk;
-        const int64_t obase = ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk;
+        const bool dense_in = (P.in.dense[b] & 3) == 3;
+        const bool dense_out = (P.out.dense[b] & 1) != 0;
+        const bool bulk = dense_in && a0 == 0;  // halo rows are contiguous runs in HBM
+        const bool full = e0 == TX && e1 == TY;
+        const int64_t ibase = ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * NV;
+        const int64_t obase = ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * NV;
         const int64_t okeep = (int64_t)P.out.base[b];
 
-        auto issue_plane = [&](int it) {
-            if (it < nplanes) {
-                const int pz = wrapi(it - kHalo, n2);
-                float* st = stage + (it % NST) * STAGE;
-                for (int cidx = tid; cidx < EX * EY; cidx += NT) {
-                    int u1 = cidx / EX, u0 = cidx - u1 * EX;
-                    int x, y, z;
-                    to_phys(P.ax, wrapi(t0 - kHalo + u0, n0), wrapi(t1 - kHalo + u1, n1), pz, x, y, z);
-                    int64_t row = y + (int64_t)G.n[1] * z;
-                    int64_t r = cell_rank(P.in, G, b, x, row, true);
-                    const float* src = r >= 0 ? P.in.pool + ibase + r * kChunk : P.in.pool;
-                    float* dstp = st + u1 * SROW + u0 * kChunk;
-                    int nb = r >= 0 ? 16 : 0;
+        // contiguous runs of a halo row along axis 0 (split at the periodic wrap)
+        if (tid == 0 && bulk) {
+            int u0 = 0, nr = 0;
+            while (u0 < EX) {
+                const int x = wrapi(t0 - H + u0, n0);
+                const int len = min(EX - u0, n0 - x);
+                s_run[nr][0] = u0;
+                s_run[nr][1] = x;
+                s_run[nr][2] = len;
+                nr++;
+                u0 += len;
+            }
+            s_nrun = nr;
+        }
+        // wrapped halo coordinates of sweep axes 0 and 1, split into x and row parts
+        if (tid < EX) {
+            int c = wrapi(t0 - H + tid, n0);
+            px0[tid] = xpart(a0, c);
+            pr0[tid] = rpart(a0, c, ny);
+        } else if (tid >= 32 && tid < 32 + EY) {
+            int u = tid - 32;
+            int c = wrapi(t1 - H + u, n1);
+            px1[u] = xpart(a1, c);
+            pr1[u] = rpart(a1, c, ny);
+        }
+
+        // sweep constants of this thread's velocity cell (chunk q = vz plane, v = vx + 4 vy)
+        const int bc[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
+        const int wi[3] = {v & 3, v >> 2, q};
+        WalkConst kw[3];
+        SweepConst ks2;
 #pragma unroll
-                    for (int j = 0; j < 4; j++) cp_async16(dstp + 4 * j, src + 4 * j, nb);
+        for (int j = 0; j < 3; j++) {
+            const int d = P.ax[j];
+            const int iv = (d == 0 ? bc[0] : d == 1 ? bc[1] : bc[2]) * 4 + (d == 0 ? wi[0] : d == 1 ? wi[1] : wi[2]);
+            const float4 c4 = P.walk[d * P.nvmax + iv];
+            kw[j] = WalkConst{c4.x, c4.y, c4.z, c4.w != 0.0f ? 1 : 0};
+            if (j == 2) {
+                const float4 s4 = P.sweep[d * P.nvmax + iv];
+                ks2 = SweepConst{s4.x, s4.y, s4.z, s4.w != 0.0f ? 1 : 0};
+            }
+        }
+        const bool zup = kw[2].up != 0;  // uniform over the item when kZUni
+        // streamed plane of step s and the output plane it completes
+        auto plane_of = [&](int s) { return kZUni ? (zup ? s - H : n2 + 2 - s) : s - H; };
+        auto out_of = [&](int s) { return kZUni ? (zup ? s - 5 : n2 + 4 - s) : s - 6; };
+        __syncthreads();  // tables ready
+
+        // ---- staging of plane s into stage s % NST --------------------------------
+        auto issue_plane = [&](int s) {
+            if (s < nsteps) {
+                const int pz = wrapi(plane_of(s), n2);
+                const int x2 = xpart(a2, pz), r2 = rpart(a2, pz, ny);
+                float* st = stage + (s % NST) * S::STAGE;
+                if (bulk) {
+                    // one lane expects the plane's bytes, then lane u1 copies halo row u1
+                    // as one bulk copy per contiguous run
+                    uint64_t* bar = &s_bar[(gstep + s) % NST];
+                    if (ltid == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        mbar_expect_tx(bar, (unsigned)(EX * EY * NV * 4));
+                    }
+                    __syncwarp();
+                    if (ltid < EY) {
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        const int64_t row = (int64_t)pr1[ltid] + r2;
+                        const float* src = P.in.pool + ibase + row * G.n[0] * NV;
+                        float* dst = st + ltid * SROW;
+                        for (int k = 0; k < s_nrun; k++)
+                            bulk_g2s(dst + s_run[k][0] * NV, src + s_run[k][1] * NV,
+                                     (unsigned)(s_run[k][2] * NV * 4), bar);
+                    }
+                } else {
+                    for (int k = ltid; k < EX * EY * 4; k += NLD) {
+                        int cell = k >> 2, piece = k & 3;
+                        int u1 = cell / EX, u0 = cell - u1 * EX;
+                        int x = px0[u0] + px1[u1] + x2;
+                        int64_t row = (int64_t)pr0[u0] + pr1[u1] + r2;
+                        int64_t r = dense_in ? row * G.n[0] + x : cell_rank(P.in, G, b, x, row, true);
+                        const float* src = r >= 0 ? P.in.pool + ibase + r * NV + 4 * piece : P.in.pool;
+                        cp_async16(st + u1 * SROW + u0 * NV + 4 * piece, src, r >= 0 ? 16 : 0);
+                    }
                 }
             }
             cp_async_commit();
         };
-
-        Slide<kLim> zs[TY];
-#pragma unroll
-        for (int j = 0; j < TY; j++) zs[j].reset();
-        float msum = 0.0f;
-        double mass = 0.0;
-
-#pragma unroll
-        for (int it = 0; it < NST - 1; it++) issue_plane(it);
-
-        for (int it = 0; it < nplanes; it++) {
-            issue_plane(it + NST - 1);
-            // ranks of the output plane (it - 6) in the next layout
-            const int k = it - 2 * kHalo;
-            if (k >= 0 && tid < TX * TY) {
-                int j = tid / TX, i = tid - j * TX;
+        auto wait_plane = [&](int s) {
+            if (bulk) {
+                uint64_t* bar = &s_bar[(gstep + s) % NST];
+                const unsigned parity = ((gstep + s) / NST) & 1u;
+                unsigned polls = 0;
+                while (!mbar_try_wait(bar, parity)) {
+                    if (++polls > kMaxPolls) {
+                        atomicOr(&P.ctr->error, 4);
+                        break;
+                    }
+                }
+            } else if (loader) {
+                cp_async_wait<NST - 2>();
+            }
+        };
+        auto out_ranks = [&](int s) {  // sparse output slots of the plane completed at s
+            const int zo = out_of(s);
+            if (dense_out || s < FIRST || zo < 0 || zo >= n2) return;
+            for (int c = ltid; c < TX * TY; c += NLD) {
+                int j = c / TX, i = c - j * TX;
                 int r = -1;
                 if (i < e0 && j < e1) {
-                    int x, y, z;
-                    to_phys(P.ax, t0 + i, t1 + j, k, x, y, z);
-                    r = (int)cell_rank(P.out, G, b, x, y + (int64_t)G.n[1] * z, false);
+                    int x = xpart(a0, t0 + i) + xpart(a1, t1 + j) + xpart(a2, zo);
+                    int64_t row = (int64_t)rpart(a0, t0 + i, ny) + rpart(a1, t1 + j, ny) + rpart(a2, zo, ny);
+                    r = (int)cell_rank(P.out, G, b, x, row, false);
                 }
-                orank[(it & 1) * TX * TY + tid] = r;
+                orank[(s & 1) * TX * TY + c] = r;
             }
-            cp_async_wait<NST - 1>();
-            __syncthreads();
+        };
+        auto keep_flags = [&](int s) {  // per-chunk keep flags of the plane completed at s
+            const int zo = out_of(s);
+            if (s < FIRST || zo < 0 || zo >= n2) return;
+            const unsigned* km = kb + (s & 1) * 16;
+            for (int c = ltid; c < TX * TY; c += NLD) {
+                int j = c / TX, i = c - j * TX;
+                if (i >= e0 || j >= e1) continue;
+                int64_t r;
+                if (dense_out) {
+                    int x = xpart(a0, t0 + i) + xpart(a1, t1 + j) + xpart(a2, zo);
+                    int64_t row = (int64_t)rpart(a0, t0 + i, ny) + rpart(a1, t1 + j, ny) + rpart(a2, zo, ny);
+                    r = row * G.n[0] + x;
+                } else {
+                    r = orank[(s & 1) * TX * TY + c];
+                }
+                if (r < 0) continue;
+                int hh = j / L, jj = j - hh * L;
+                if ((km[hh * 8 + (i >> 1)] >> (16 * (i & 1) + jj)) & 1u) P.keepq[(okeep + r) * 4 + q] = 1;
+            }
+        };
 
-            // sweep 0 along axis 0 on all EY halo rows
-            const float* st = stage + (it % NST) * STAGE;
-            if (hi < EY) {
-                Slide<kLim> s;
-                s.reset();
-                const float* line = st + hi * SROW + v;
-                float* xo = xbuf + hi * XROW + v;
+        const bool cvalid = ci < e0;
+        Walk<kLim> zu[kZUni ? L : 1];
+        Slide<kLim> zg[kZUni ? 1 : L];
 #pragma unroll
-                for (int u = 0; u < EX; u++) {
-                    float res = s.push(line[u * kChunk], kc[0]);
-                    if (u >= 2 * kHalo) xo[(u - 2 * kHalo) * kChunk] = res;
-                }
-            }
-            __syncthreads();
+        for (int j = 0; j < (kZUni ? L : 1); j++) zu[j].reset();
+#pragma unroll
+        for (int j = 0; j < (kZUni ? 1 : L); j++) zg[j].reset();
+        float msum = 0.0f, mcomp = 0.0f;  // Kahan-compensated FP32 mass of this thread
 
-            // sweep 1 along axis 1 for tile column `hi`, then sweep 2 (streamed)
-            float col[TY];
-            {
-                Slide<kLim> s;
-                s.reset();
-                const float* line = xbuf + hi * kChunk + v;
-#pragma unroll
-                for (int r = 0; r < EY; r++) {
-                    float res = s.push(line[r * XROW], kc[1]);
-                    if (r >= 2 * kHalo) col[r - 2 * kHalo] = res;
-                }
-            }
-            const int* orow = orank + (it & 1) * TX * TY;
-#pragma unroll
-            for (int j = 0; j < TY; j++) {
-                float res = zs[j].push(col[j], kc[2]);
-                if (k >= 0) {
-                    int r = orow[j * TX + hi];
-                    if (r >= 0) {
-                        P.out.pool[obase + (int64_t)r * kChunk + v] = res;
-                        msum += res;
-                    }
-                    unsigned m = __ballot_sync(0xffffffffu, r >= 0 && res >= P.thr);
-                    if (r >= 0 && v == 0) {
-                        unsigned half = (tid & 16) ? (m >> 16) : (m & 0xffffu);
-                        P.keepq[(okeep + r) * 4 + q] = half ? 1 : 0;
-                    }
-                }
-            }
-            mass += (double)msum;
-            msum = 0.0f;
+        if (loader) {
+            issue_plane(0);
+            issue_plane(1);
         }
+
+        // one streamed plane; kEmit: the plane completes an output plane
+        auto step = [&](int s, auto emit_tag) {
+            constexpr bool kEmit = decltype(emit_tag)::value;
+            wait_plane(s);
+            __syncthreads();  // plane s staged; previous readers of xbuf done
+            if (!loader) {
+                // sweep 0 along axis 0 on halo row `hi`
+                const float* line = stage + (s % NST) * S::STAGE + hi * SROW + v;
+                float* xo = xbuf + hi * XROW + v;
+                Walk<kLim> wk;
+                wk.reset();
+                if (kw[0].up) {
+#pragma unroll
+                    for (int t = 0; t < TX + 5; t++) {
+                        float r = wk.push(line[t * NV], kw[0]);
+                        if (t >= 5) xo[(t - 5) * NV] = r;
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < TX + 5; t++) {
+                        float r = wk.push(line[(TX + 5 - t) * NV], kw[0]);
+                        if (t >= 5) xo[(TX + 4 - t) * NV] = r;
+                    }
+                }
+            } else {
+                keep_flags(s - 1);
+                out_ranks(s + 1);
+                issue_plane(s + NST - 1);
+            }
+            __syncthreads();  // sweep-0 rows complete
+            // sweep 1 along axis 1 over rows j0..j0+L-1 of tile column ci, each output
+            // pushed straight into the streamed window of its cell (sweep 2)
+            const int zo = out_of(s);
+            float* dst = P.out.pool + obase + v +
+                         ((int64_t)(t0 + ci) * P.stride[a0] + (int64_t)(t1 + j0) * P.stride[a1] +
+                          (int64_t)zo * P.stride[a2]) * NV;
+            const int64_t dstep = P.stride[a1] * NV;
+            const bool fast = dense_out && full;
+            const int* orow = orank + (s & 1) * TX * TY + j0 * TX + ci;
+            float psum = 0.0f;
+            unsigned kmask = 0;
+            auto consume = [&](int jj, float yv) {
+                float res;
+                if (kZUni) res = zu[kZUni ? jj : 0].push(yv, kw[2]);
+                else res = zg[kZUni ? 0 : jj].push(yv, ks2);
+                if (kEmit) {
+                    if (fast) {
+                        dst[jj * dstep] = res;
+                        psum += res;
+                    } else {
+                        int64_t r = -1;
+                        if (dense_out) {
+                            if (cvalid && j0 + jj < e1) r = 0;
+                        } else {
+                            r = orow[jj * TX];
+                        }
+                        if (r >= 0) {
+                            if (dense_out) dst[jj * dstep] = res;
+                            else P.out.pool[obase + r * NV + v] = res;
+                            psum += res;
+                        }
+                    }
+                    if (res >= P.thr) kmask |= 1u << jj;
+                }
+            };
+            const float* line = xbuf + (j0 * XROW) + ci * NV + v;
+            Walk<kLim> wk;
+            wk.reset();
+            if (kw[1].up) {
+#pragma unroll
+                for (int t = 0; t < L + 5; t++) {
+                    float r = wk.push(line[t * XROW], kw[1]);
+                    if (t >= 5) consume(t - 5, r);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < L + 5; t++) {
+                    float r = wk.push(line[(L + 5 - t) * XROW], kw[1]);
+                    if (t >= 5) consume(L + 4 - t, r);
+                }
+            }
+            if (kEmit) {
+                unsigned km = __reduce_or_sync(0xffffffffu, kmask << (16 * (ci & 1)));
+                if (lane == 0) kb[(s & 1) * 16 + warp] = km;
+                float y = psum - mcomp;
+                float t = msum + y;
+                mcomp = (t - msum) - y;
+                msum = t;
+            }
+        };
+        int s = 0;
+        for (; s < FIRST; s++) step(s, std::false_type{});
+        for (; s < nsteps; s++) step(s, std::true_type{});
+
+        __syncthreads();
+        if (loader) keep_flags(nsteps - 1);
         cp_async_wait<0>();
-        for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
-        if ((tid & 31) == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
+        if (bulk) gstep += (unsigned)nsteps;
+        double m = (double)msum;
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0 && m != 0.0) atomicAdd(&P.ctr->mass, m);
     }
 }
 
@@ -231,6 +457,7 @@ struct TileArgs {
     const uint64_t* ubits;
     int ax[3];
     int ntile0, ntile1;
+    int ty;
 };
 
 __device__ bool row_any(const uint64_t* rowp, int xlo, int xhi)
@@ -257,8 +484,8 @@ __global__ void k_tile_flags(TileArgs T, uint32_t* __restrict__ flags)
     int lo[3], hi[3];
     lo[T.ax[0]] = (tile % T.ntile0) * TX;
     hi[T.ax[0]] = min(lo[T.ax[0]] + TX, G.n[T.ax[0]]);
-    lo[T.ax[1]] = (tile / T.ntile0) * TY;
-    hi[T.ax[1]] = min(lo[T.ax[1]] + TY, G.n[T.ax[1]]);
+    lo[T.ax[1]] = (tile / T.ntile0) * T.ty;
+    hi[T.ax[1]] = min(lo[T.ax[1]] + T.ty, G.n[T.ax[1]]);
     lo[T.ax[2]] = 0;
     hi[T.ax[2]] = G.n[T.ax[2]];
     const uint64_t* seg = T.ubits + (int64_t)b * G.RW;
@@ -282,6 +509,23 @@ __global__ void k_tile_items(int64_t ntiles, int nb, const uint32_t* __restrict_
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+template <int TY, bool kLim, bool kZUni>
+vl_status launch_fused(Grid* g, const FusedArgs& P)
+{
+    auto kern = k_fused<TY, kLim, kZUni>;
+    const int smem = Shape<TY>::SMEM;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int nsm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (per_sm < 1) per_sm = 1;
+    kern<<<nsm * per_sm, NT, smem, g->stream>>>(P);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(g, e, "fused sweep launch");
+    return VL_OK;
+}
+
 }  // namespace
 
 vl_status run_fused(Grid* g, const StepArgs& a)
@@ -290,8 +534,10 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     Layout& A = g->lay[g->cur];
     Layout& B = g->lay[1 - g->cur];
     int ax[3] = {a.order[0], a.order[1], a.order[2]};
+    const bool zuni = ax[2] == 2;  // the streamed axis is the chunk's (vz) axis
+    const int ty = zuni ? 16 : 8;
     int ntile0 = (G.n[ax[0]] + TX - 1) / TX;
-    int ntile1 = (G.n[ax[1]] + TY - 1) / TY;
+    int ntile1 = (G.n[ax[1]] + ty - 1) / ty;
     int64_t ntiles = (int64_t)ntile0 * ntile1;
     if (ntiles > 0xffffffffLL) return fail(g, VL_EINVAL, "fused form: too many tiles");
     int64_t need = ntiles * G.nb;
@@ -314,54 +560,38 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     for (int j = 0; j < 3; j++) T.ax[j] = ax[j];
     T.ntile0 = ntile0;
     T.ntile1 = ntile1;
-    k_tile_flags<<<nblk(need, 256), 256, 0, g->stream>>>(T, g->tile_flags); note_launch();
+    T.ty = ty;
+    k_tile_flags<<<nblk(need, 256), 256, 0, g->stream>>>(T, g->tile_flags);
+    note_launch();
     launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, G.nb, g->stream);
     launch_base_scan(g->item_cnt, g->item_base, G.nb, g->stream);
     k_tile_items<<<nblk(need, 256), 256, 0, g->stream>>>(ntiles, G.nb, g->tile_flags, g->tile_pos,
-                                                           g->item_base, g->items); note_launch();
+                                                           g->item_base, g->items);
+    note_launch();
 
     FusedArgs P;
     P.G = G;
     P.in = A.view();
     P.out = B.view();
-    for (int j = 0; j < 3; j++) {
-        P.ax[j] = ax[j];
-        P.cs[j] = a.c_scale[ax[j]];
-        P.vmin[j] = g->vmesh.vmin[j];
-        P.dv[j] = g->vmesh.dv[j];
-    }
+    P.stride[0] = 1;
+    P.stride[1] = G.n[0];
+    P.stride[2] = (int64_t)G.n[0] * G.n[1];
+    for (int j = 0; j < 3; j++) P.ax[j] = ax[j];
+    P.walk = a.walk;
+    P.sweep = a.sweep;
+    P.nvmax = a.nvmax;
     P.thr = (float)g->threshold;
     P.ntile0 = ntile0;
     P.items = g->items;
     P.item_base = g->item_base;
     P.keepq = B.keepq;
     P.ctr = g->counters;
-    static int configured = 0;
-    if (!configured) {
-        cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        configured = 1;
-    }
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
-    int per_sm = 0;
-    if (a.limiter)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<true>, NT, kSmemBytes);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, NT, kSmemBytes);
-    if (per_sm < 1) per_sm = 1;
-    int grid = nsm * per_sm;
     cudaEventRecord(g->ev_sweep0, g->stream);
-    if (a.limiter) {
-        k_fused<true><<<grid, NT, kSmemBytes, g->stream>>>(P); note_launch();
-    }
-    else {
-        k_fused<false><<<grid, NT, kSmemBytes, g->stream>>>(P); note_launch();
-    }
+    vl_status st;
+    if (zuni) st = a.limiter ? launch_fused<16, true, true>(g, P) : launch_fused<16, false, true>(g, P);
+    else st = a.limiter ? launch_fused<8, true, false>(g, P) : launch_fused<8, false, false>(g, P);
     cudaEventRecord(g->ev_sweep1, g->stream);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(g, e, "fused sweep launch");
-    return VL_OK;
+    return st;
 }
 
 }  // namespace vlgt

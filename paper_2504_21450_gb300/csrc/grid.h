@@ -54,6 +54,9 @@ struct Grid {
     int64_t ntiles_alloc = 0;
     int64_t item_mass_alloc = 0;
     int64_t* host_scalar = nullptr;       // pinned
+    float4* ctab = nullptr;               // device [2][3][nvmax] sweep constants
+    float4* ctab_host = nullptr;          // pinned staging of the same
+    double ctab_dt = -1.0;                // dt the table was built for
 
     vl_step_stats stats{};
     int64_t launches = 0;                 // kernels launched by the library (running count)
@@ -105,6 +108,9 @@ struct StepArgs {
     int order[3];       // physical axis of sweep j
     int limiter;
     int tile[2];
+    const float4* walk;   // device [3][nvmax]: WalkConst per axis and velocity index
+    const float4* sweep;  // device [3][nvmax]: SweepConst per axis and velocity index
+    int nvmax;
 };
 vl_status run_fused(Grid* g, const StepArgs& a);
 vl_status run_3pass(Grid* g, const StepArgs& a);

@@ -6,9 +6,10 @@
 // Pass 1 reads the current layout (present blocks only) and writes every slot of the
 // next layout (the 27-cell union); passes 2 and 3 update the next layout in place.  One
 // thread walks one periodic pencil for one velocity cell with the sliding-window PPM
-// remap; the 64 threads of a block id cover its 64 velocity cells, so every step of a
-// walk is a coalesced load of 2 x 64 bytes per warp.  The last pass also raises the
-// per-chunk keep flags of the sparsity rule and sums the mass.
+// remap (Walk, from the upwind end of the pencil); the 64 threads of a block id cover
+// its 64 velocity cells, so every step of a walk is a coalesced load of 2 x 64 bytes
+// per warp.  The last pass also raises the per-chunk keep flags of the sparsity rule
+// (set-only: the flags are cleared before the step) and sums the mass.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -94,63 +95,74 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     int bc[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
     int within[3] = {v & 3, (v >> 2) & 3, v >> 4};
     int iv = bc[P.dim] * 4 + within[P.dim];
-    const SweepConst kc = sweep_const((P.vmin + (iv + 0.5) * P.dv) * P.cs);
+    const WalkConst kc = walk_const((P.vmin + (iv + 0.5) * P.dv) * P.cs);
+    const bool up = kc.up != 0;
+    // the warp's velocity cells move the same way unless the block straddles v_d = 0
+    const bool uni = __all_sync(0xffffffffu, up) || __all_sync(0xffffffffu, !up);
 
     const float* src = P.in.pool + ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + l;
     float* dst = P.out.pool + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + l;
     const int* rin = s_rin[k];
     const int* rout = s_rout[k];
-    auto load = [&](int w) -> float {
-        int r = rin[w];
+    // the walk runs from the upwind end: walking position m is cell m (c >= 0) or
+    // cell nd-1-m (c < 0)
+    auto cell_at = [&](int m) { return up ? m : nd - 1 - m; };
+    auto load = [&](int m) -> float {
+        int r = rin[cell_at(m)];
         return r >= 0 ? src[(int64_t)r * kChunk] : 0.0f;
     };
-    // originals of the cells that the wrapped tail reads again after they were written
-    const float t0 = load(0), t1 = load(1 % nd), t2 = load(2 % nd);
+    // originals of walking positions 0 and 1, read again by the wrapped tail after
+    // they were updated in place
+    const float t0 = load(0), t1 = load(1 % nd);
 
-    Slide<kLim> s;
+    Walk<kLim> s;
     s.reset();
     float msum = 0.0f;
     double mass = 0.0;
     const float thr = P.thr;
-    auto emit = [&](int kk, float res) {
-        int r = rout[kk];
+    auto emit = [&](int mm, float res) {  // new average of walking position mm
+        int c = cell_at(mm);
+        int r = rout[c];
         if (r >= 0) dst[(int64_t)r * kChunk] = res;
         if (P.last) {
             bool keep = r >= 0 && res >= thr;
-            unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (r >= 0 && (threadIdx.x & 15) == 0) {
+            uint8_t* kq = P.keepq + ((int64_t)P.out.base[b] + r) * 4 + q;
+            if (uni) {
+                unsigned m = __ballot_sync(0xffffffffu, keep);
                 unsigned half = (threadIdx.x & 16) ? (m >> 16) : (m & 0xffffu);
-                P.keepq[((int64_t)P.out.base[b] + r) * 4 + q] = half ? 1 : 0;
+                if (half && (threadIdx.x & 15) == 0) *kq = 1;
+            } else if (keep) {
+                *kq = 1;
             }
             if (r >= 0) msum += res;
         }
     };
-    int i = -3;
-    for (; i < 0; i++) s.push(load(wrapi(i, nd)), kc);
+    int m = -3;
+    for (; m < 0; m++) s.push(load(wrapi(m, nd)), kc);
     // main walk, loads batched ahead of the dependent arithmetic
-    for (; i + 8 <= nd; i += 8) {
+    for (; m + 8 <= nd; m += 8) {
         float a[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) a[u] = load(i + u);
+        for (int u = 0; u < 8; u++) a[u] = load(m + u);
 #pragma unroll
         for (int u = 0; u < 8; u++) {
             float res = s.push(a[u], kc);
-            if (i + u >= 3) emit(i + u - 3, res);
+            if (m + u >= 2) emit(m + u - 2, res);
         }
         if (P.last) {
             mass += (double)msum;
             msum = 0.0f;
         }
     }
-    for (; i < nd; i++) {
-        float res = s.push(load(i), kc);
-        if (i >= 3) emit(i - 3, res);
+    for (; m < nd; m++) {
+        float res = s.push(load(m), kc);
+        if (m >= 2) emit(m - 2, res);
     }
-    const float tail[3] = {t0, t1, t2};
+    const float tail[2] = {t0, t1};
 #pragma unroll
-    for (int u = 0; u < 3; u++, i++) {
+    for (int u = 0; u < 2; u++, m++) {
         float res = s.push(tail[u], kc);
-        if (i >= 3) emit(i - 3, res);
+        if (m >= 2) emit(m - 2, res);
     }
     if (P.last) {
         mass += (double)msum;
