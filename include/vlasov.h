@@ -181,6 +181,39 @@ vl_status vl_mass(vl_grid* grid, double* mass);
 /* Counters of the last vl_translate (synchronises). */
 vl_status vl_stats(vl_grid* grid, vl_step_stats* stats);
 
+/* One translation step that allocates no device memory.
+ *
+ * The paper has no counterpart to this call: it exists for callers that cannot allocate,
+ * such as code running inside a CUDA graph capture region, a runtime that owns the whole
+ * device memory budget, or an embedding host whose allocator this library cannot reach.
+ *
+ * It runs the fused Ghost Translation kernel (the three PPM sweeps, Section 3) once on a
+ * DENSE velocity space (every cell holds every block id), without the sparsity rule.
+ * f_in and f_out are device pointers owned by the caller, each
+ * (nv[0]/4)*(nv[1]/4)*(nv[2]/4) * ncells * 64 floats, in the library's storage order:
+ * f[((b*4 + q)*ncells + c)*16 + l] for block id b, vz index q within the block, cell c
+ * and in-plane index l = vx + 4*vy within the block.  They must not overlap.  *mass_out
+ * (device pointer) receives the FP64 total mass of f_out (sum of values times
+ * dx^3 dv^3).  Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * of the current device; the call does not synchronise.
+ *
+ * Everything else the kernel needs (work list, layout tables, sweep constants, counters)
+ * lives in one static device array of VL_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.  The first call on a device looks
+ * up that array's device address (setup); make that first call before any stream
+ * capture.  All calls share the array and each one overwrites it, so calls whose work
+ * overlaps on the GPU (on different streams, or from different host threads) race: order
+ * them on one stream.
+ * Errors: VL_EINVAL (null pointer, bad descriptor or order, f_in == f_out), VL_ECFL,
+ * VL_ECAPACITY (the work list of this grid does not fit in the static array: at most
+ * about 1 MiB for nb*(21 + 4*tiles) bytes, with tiles = ceil(n_a/16)*ceil(n_b/TY) over
+ * the first two sweep axes, TY = 16 when the order ends in z, else 8), VL_ECUDA. */
+#define VL_NOALLOC_SCRATCH_BYTES (1u << 20)
+vl_status vl_translate_dense_noalloc(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
+                                     double dt, const char* order, int limiter,
+                                     const float* f_in, float* f_out, double* mass_out,
+                                     void* stream);
+
 const char* vl_status_str(vl_status status);
 const char* vl_last_error(const vl_grid* grid);
 

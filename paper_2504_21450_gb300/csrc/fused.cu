@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <type_traits>
 
 #include "grid.h"
@@ -593,5 +594,41 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     cudaEventRecord(g->ev_sweep1, g->stream);
     return st;
 }
+
+// Launch of the fused kernel over caller-provided buffers of a dense layout (every
+// cell holds every block id): `in`/`out` carry cnt/base/dense arrays and pools, items and
+// item_base list every (block id, tile) pair, ctab holds the constant tables.  Used by the
+// allocation-free entry point; the step's sparsity rule is not applied (threshold +inf).
+vl_status launch_fused_dense(const GridGeom& G, const LayoutView& in, const LayoutView& out,
+                             const int order[3], int limiter, const float4* ctab, int nvmax,
+                             const uint32_t* items, const int64_t* item_base, int ntile0,
+                             StepCounters* ctr, int device, cudaStream_t stream)
+{
+    FusedArgs P;
+    P.G = G;
+    P.in = in;
+    P.out = out;
+    P.stride[0] = 1;
+    P.stride[1] = G.n[0];
+    P.stride[2] = (int64_t)G.n[0] * G.n[1];
+    for (int j = 0; j < 3; j++) P.ax[j] = order[j];
+    P.walk = ctab;
+    P.sweep = ctab + 3 * nvmax;
+    P.nvmax = nvmax;
+    P.thr = INFINITY;
+    P.ntile0 = ntile0;
+    P.items = items;
+    P.item_base = item_base;
+    P.keepq = nullptr;
+    P.ctr = ctr;
+    Grid tmp;  // launch helper needs the device and the stream only
+    tmp.dev.device = device;
+    tmp.stream = stream;
+    const bool zuni = order[2] == 2;
+    if (zuni) return limiter ? launch_fused<16, true, true>(&tmp, P) : launch_fused<16, false, true>(&tmp, P);
+    return limiter ? launch_fused<8, true, false>(&tmp, P) : launch_fused<8, false, false>(&tmp, P);
+}
+
+int fused_tile_rows(const int order[3]) { return order[2] == 2 ? 16 : 8; }
 
 }  // namespace vlgt

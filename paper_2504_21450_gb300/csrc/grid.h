@@ -115,5 +115,11 @@ struct StepArgs {
 vl_status run_fused(Grid* g, const StepArgs& a);
 vl_status run_3pass(Grid* g, const StepArgs& a);
 vl_status fused_prepare(Grid* g, const StepArgs& a, int64_t* nwork);
+vl_status launch_fused_dense(const GridGeom& G, const LayoutView& in, const LayoutView& out,
+                             const int order[3], int limiter, const float4* ctab, int nvmax,
+                             const uint32_t* items, const int64_t* item_base, int ntile0,
+                             StepCounters* ctr, int device, cudaStream_t stream);
+int fused_tile_rows(const int order[3]);
+constexpr int kFusedTileX = 16;
 
 }  // namespace vlgt

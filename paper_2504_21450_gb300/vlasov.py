@@ -88,6 +88,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "vl_moments": (i, [p, p, i]),
         "vl_mass": (i, [p, p]),
         "vl_stats": (i, [p, p]),
+        "vl_translate_dense_noalloc": (i, [p, p, d, ctypes.c_char_p, i, p, p, p, p]),
         "vl_status_str": (ctypes.c_char_p, [i]),
         "vl_last_error": (ctypes.c_char_p, [p]),
     }
@@ -186,6 +187,15 @@ def vl_stats(grid) -> vl_step_stats:
     s = vl_step_stats()
     _check(load().vl_stats(grid, ctypes.byref(s)), "vl_stats", grid)
     return s
+
+
+def vl_translate_dense_noalloc(space: vl_space_desc, vmesh: vl_vmesh_desc, dt: float, order: str,
+                               limiter: int, f_in_ptr: int, f_out_ptr: int, mass_out_ptr: int,
+                               stream_ptr: int) -> int:
+    """Returns the status code (no exception: the caller decides)."""
+    return load().vl_translate_dense_noalloc(ctypes.byref(space), ctypes.byref(vmesh), float(dt),
+                                             order.encode(), int(limiter), f_in_ptr, f_out_ptr,
+                                             mass_out_ptr, stream_ptr)
 
 
 # Convenience object -------------------------------------------------------------------
