@@ -103,7 +103,15 @@ typedef struct {
     int ghost;      /* ghost-layer depth k of GT-k; only 3 (exact) is implemented */
     int tile[2];    /* fused tile extent along the first two sweep axes; 0 = default */
     int check;      /* 1: synchronise after the call and report device-side errors */
-    int reserved[8];
+    int graph;      /* 1: run the nsteps steps as one captured CUDA graph with no host
+                       synchronisation between steps (the graph is cached and replayed
+                       by later calls with the same arguments); the pools are sized to
+                       `capacity` blocks beforehand, a step that would need more is
+                       detected on the device, the state stays at the last complete
+                       step, the capacity grows and the remaining steps run again */
+    int reserved0;
+    int64_t capacity; /* graph mode: blocks per layout; 0 = 1.25 x the current slots */
+    int reserved[4];
 } vl_translate_opts;
 
 /* Counters of the last vl_translate call (FP64 sums on the device). */
@@ -120,6 +128,9 @@ typedef struct {
     double index_ms;        /* block union, slot indexing and work lists */
     double prune_ms;        /* sparsity rule and dropped-mass accounting */
     int64_t launches;       /* kernels the library launched during the call */
+    int64_t graph_replays;  /* graph mode: captured sequences launched (incl. re-runs) */
+    int64_t capacity_regrows; /* graph mode: capacity overflows recovered from */
+    int64_t capacity;       /* graph mode: blocks per layout at the end of the call */
 } vl_step_stats;
 
 void vl_translate_opts_default(vl_translate_opts* opts);

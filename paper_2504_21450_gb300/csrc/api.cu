@@ -84,6 +84,232 @@ vl_status parse_order(const char* order, int out[3])
     return VL_OK;
 }
 
+
+// Physical volume of one phase-space cell (dx^3 dv^3).
+double phase_volume(const Grid* g)
+{
+    return g->space.dx[0] * g->space.dx[1] * g->space.dx[2] * g->vmesh.dv[0] * g->vmesh.dv[1] *
+           g->vmesh.dv[2];
+}
+
+void add_step(const Grid* g, const StepCounters& C, vl_step_stats* S)
+{
+    const double vol = phase_volume(g);
+    S->steps++;
+    S->union_blocks = (int64_t)C.needed;
+    S->blocks = (int64_t)C.kept;
+    S->dropped_blocks = (int64_t)C.dropped;
+    S->dropped_mass += C.dropped_mass * vol;
+    S->mass = (C.mass - C.dropped_mass) * vol;
+}
+
+// One step from lay[cur] into lay[1-cur], queued on g->stream.  Graph mode: nothing here
+// synchronises or allocates; the pools already hold `capacity` blocks and the step checks
+// that bound on the device.  Otherwise the slot total is read back and the output pool
+// grown to fit.
+vl_status enqueue_step(Grid* g, StepArgs a, bool fused, bool graph, int64_t capacity, StepCounters* ctr)
+{
+    Layout& A = g->lay[g->cur];
+    Layout& B = g->lay[1 - g->cur];
+    a.ctr = ctr;
+    a.time_phases = !graph;
+    cudaMemsetAsync(ctr, 0, sizeof(StepCounters), g->stream);
+    launch_union(g, A, B);
+    if (graph) {
+        launch_index(g, B);
+        launch_capacity_check(g, B, capacity, ctr);
+        cudaMemsetAsync(B.keepq, 0, (size_t)capacity * 4, g->stream);
+    } else {
+        int64_t total = 0;
+        vl_status st = layout_index(g, B, &total);
+        if (st != VL_OK) return st;
+        st = layout_ensure_pool(g, B, std::max<int64_t>(total, 1));
+        if (st != VL_OK) return st;
+        cudaMemcpyAsync(&ctr->needed, B.base + g->geom.nb, 8, cudaMemcpyDeviceToDevice, g->stream);
+        cudaMemsetAsync(B.keepq, 0, (size_t)std::max<int64_t>(total, 1) * 4, g->stream);
+    }
+    vl_status st = fused ? run_fused(g, a) : run_3pass(g, a);
+    if (st != VL_OK) return st;
+    launch_pack_keep(g, B, ctr);
+    return VL_OK;
+}
+
+vl_status step_error(Grid* g, const StepCounters& C)
+{
+    return fail(g, (C.error & 4) ? VL_ETIMEOUT : VL_ECUDA,
+                "vl_translate: device-side error flag " + std::to_string(C.error) +
+                    ((C.error & 4) ? " (a staging barrier wait ran out)" : ""));
+}
+
+// Step by step, with the counters read back after every step.
+vl_status translate_steps(Grid* g, const StepArgs& a, bool fused, int nsteps, vl_step_stats* S)
+{
+    cudaEvent_t e0, e1, ep;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&ep);
+    vl_status st = VL_OK;
+    for (int step = 0; step < nsteps && st == VL_OK; step++) {
+        cudaEventRecord(e0, g->stream);
+        st = enqueue_step(g, a, fused, false, 0, g->counters);
+        if (st != VL_OK) break;
+        cudaEventRecord(e1, g->stream);
+        cudaMemcpyAsync(g->counters_host, g->counters, sizeof(StepCounters), cudaMemcpyDeviceToHost,
+                        g->stream);
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(g, e, "vl_translate step");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        S->device_ms += ms;
+        cudaEventElapsedTime(&ms, g->ev_sweep0, g->ev_sweep1);
+        S->sweep_ms += ms;
+        cudaEventElapsedTime(&ms, e0, g->ev_sweep0);
+        S->index_ms += ms;
+        cudaEventElapsedTime(&ms, g->ev_sweep1, e1);
+        S->prune_ms += ms;
+        const StepCounters& C = *g->counters_host;
+        if (C.error) {
+            st = step_error(g, C);
+            break;
+        }
+        add_step(g, C, S);
+        g->cur = 1 - g->cur;
+        g->lay[g->cur].total = (int64_t)C.needed;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(ep);
+    return st;
+}
+
+uint64_t mix(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+// nsteps steps as one captured CUDA graph (cached and replayed while its arguments and
+// buffers stay the same).  A step whose union needs more than `capacity` slots aborts
+// itself and every later step on the device; the state stays at the last complete step,
+// the pools grow and the remaining steps run again.
+vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t capacity, vl_step_stats* S)
+{
+    const GridGeom& G = g->geom;
+    int64_t cap = capacity > 0 ? capacity
+                               : std::max<int64_t>(g->lay[g->cur].total + g->lay[g->cur].total / 4, 1024);
+    if (!g->abort_flag) {
+        g->abort_flag = (int*)g->alloc(sizeof(int));
+        if (!g->abort_flag) return fail(g, VL_ENOMEM, "graph mode: allocation failed");
+    }
+    if (!g->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(g, e, "graph mode: stream");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    vl_status st = VL_OK;
+    int done_total = 0;
+    while (st == VL_OK && done_total < nsteps) {
+        const int n = nsteps - done_total;
+        // buffers the captured steps use, sized before capture
+        st = layout_grow_pool(g, g->lay[g->cur], cap);
+        if (st == VL_OK) st = layout_ensure_pool(g, g->lay[1 - g->cur], cap);
+        if (st == VL_OK && fused) st = fused_worklist_alloc(g, a);
+        if (st == VL_OK && g->step_ctr_n < n) {
+            g->release(g->step_ctr);
+            if (g->step_ctr_host) cudaFreeHost(g->step_ctr_host);
+            g->step_ctr_host = nullptr;
+            g->step_ctr = (StepCounters*)g->alloc((size_t)n * sizeof(StepCounters));
+            cudaError_t e = cudaMallocHost((void**)&g->step_ctr_host, (size_t)n * sizeof(StepCounters));
+            if (!g->step_ctr || e != cudaSuccess) st = fail(g, VL_ENOMEM, "graph mode: counter allocation failed");
+            else g->step_ctr_n = n;
+        }
+        if (st != VL_OK) break;
+        uint64_t key = 0;
+        const uint64_t parts[] = {(uint64_t)n, (uint64_t)fused, (uint64_t)a.limiter, (uint64_t)a.order[0],
+                                  (uint64_t)a.order[1], (uint64_t)a.order[2], (uint64_t)cap, (uint64_t)g->cur,
+                                  (uint64_t)(uintptr_t)g->lay[0].pool, (uint64_t)(uintptr_t)g->lay[1].pool,
+                                  (uint64_t)(uintptr_t)g->step_ctr, (uint64_t)(uintptr_t)g->items,
+                                  (uint64_t)(uintptr_t)a.walk, (uint64_t)(uintptr_t)g->stream};
+        for (uint64_t v : parts) key = mix(key, v);
+        if (!g->graph_exec || key != g->graph_key) {
+            if (g->graph_exec) {
+                cudaGraphExecDestroy(g->graph_exec);
+                g->graph_exec = nullptr;
+            }
+            cudaStream_t user = g->stream;
+            const int cur0 = g->cur;
+            const int64_t kernels0 = launch_count();
+            g->stream = g->capture_stream;
+            g->geom.abort = g->abort_flag;
+            cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) st = cuda_fail(g, e, "graph mode: begin capture");
+            if (st == VL_OK) cudaMemsetAsync(g->abort_flag, 0, sizeof(int), g->stream);
+            for (int k = 0; k < n && st == VL_OK; k++) {
+                st = enqueue_step(g, a, fused, true, cap, g->step_ctr + k);
+                g->cur = 1 - g->cur;
+            }
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+            g->stream = user;
+            g->geom.abort = nullptr;
+            g->cur = cur0;
+            if (st == VL_OK && e2 != cudaSuccess) st = cuda_fail(g, e2, "graph mode: end capture");
+            if (st == VL_OK) {
+                e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+                if (e != cudaSuccess) st = cuda_fail(g, e, "graph mode: instantiate");
+            }
+            if (graph) cudaGraphDestroy(graph);
+            if (st != VL_OK) break;
+            g->graph_key = key;
+            g->graph_kernels = launch_count() - kernels0;
+            g_launches.fetch_sub(g->graph_kernels, std::memory_order_relaxed);  // counted per replay
+        }
+        g_launches.fetch_add(g->graph_kernels, std::memory_order_relaxed);
+        cudaEventRecord(e0, g->stream);
+        cudaError_t e = cudaGraphLaunch(g->graph_exec, g->stream);
+        cudaEventRecord(e1, g->stream);
+        cudaMemcpyAsync(g->step_ctr_host, g->step_ctr, (size_t)n * sizeof(StepCounters),
+                        cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(g, e, "graph mode: launch");
+            break;
+        }
+        S->graph_replays++;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        S->device_ms += ms;
+        int d = 0;
+        while (d < n && g->step_ctr_host[d].done) {
+            add_step(g, g->step_ctr_host[d], S);
+            d++;
+        }
+        if (d > 0) {
+            g->cur = (g->cur + d) & 1;
+            g->lay[g->cur].total = (int64_t)g->step_ctr_host[d - 1].needed;
+        }
+        done_total += d;
+        if (d < n) {
+            const StepCounters& C = g->step_ctr_host[d];
+            if (C.error & 8) {
+                cap = std::max<int64_t>((int64_t)C.needed + (int64_t)C.needed / 4, cap + cap / 2);
+                S->capacity_regrows++;
+            } else {
+                st = C.error ? step_error(g, C) : fail(g, VL_ECUDA, "graph mode: step did not complete");
+            }
+        }
+    }
+    S->capacity = cap;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -225,6 +451,11 @@ vl_status vl_grid_destroy(vl_grid* grid)
     g->release(g->tile_pos);
     g->release(g->items);
     g->release(g->item_mass);
+    if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+    if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
+    g->release(g->abort_flag);
+    g->release(g->step_ctr);
+    if (g->step_ctr_host) cudaFreeHost(g->step_ctr_host);
     if (g->ev_sweep0) cudaEventDestroy(g->ev_sweep0);
     if (g->ev_sweep1) cudaEventDestroy(g->ev_sweep1);
     g->release(g->ctab);
@@ -360,79 +591,15 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
     a.tile[0] = opts.tile[0];
     a.tile[1] = opts.tile[1];
     const bool fused = opts.form != VL_FORM_3PASS;
-
-    vl_step_stats S{};
-    S.mass_before = g->stats.mass;
-    cudaEvent_t e0, e1, ei, ep;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventCreate(&ei);
-    cudaEventCreate(&ep);
     if (!g->ev_sweep0) {
         cudaEventCreate(&g->ev_sweep0);
         cudaEventCreate(&g->ev_sweep1);
     }
-    float total_ms = 0.0f, sweep_ms = 0.0f, index_ms = 0.0f, prune_ms = 0.0f;
+    vl_step_stats S{};
+    S.mass_before = g->stats.mass;
     const int64_t launches0 = launch_count();
-    vl_status st = VL_OK;
-    for (int step = 0; step < nsteps && st == VL_OK; step++) {
-        Layout& A = g->lay[g->cur];
-        Layout& B = g->lay[1 - g->cur];
-        cudaEventRecord(e0, g->stream);
-        cudaMemsetAsync(g->counters, 0, sizeof(StepCounters), g->stream);
-        launch_union(g, A, B);
-        int64_t total = 0;
-        st = layout_index(g, B, &total);
-        if (st != VL_OK) break;
-        st = layout_ensure_pool(g, B, std::max<int64_t>(total, 1));
-        if (st != VL_OK) break;
-        cudaMemsetAsync(B.keepq, 0, (size_t)std::max<int64_t>(total, 1) * 4, g->stream);
-        st = fused ? run_fused(g, a) : run_3pass(g, a);
-        if (st != VL_OK) break;
-        cudaEventRecord(ep, g->stream);
-        launch_pack_keep(g, B);
-        cudaEventRecord(e1, g->stream);
-        cudaMemcpyAsync(g->counters_host, g->counters, sizeof(StepCounters), cudaMemcpyDeviceToHost,
-                        g->stream);
-        cudaError_t e = cudaStreamSynchronize(g->stream);
-        if (e != cudaSuccess) {
-            st = cuda_fail(g, e, "vl_translate step");
-            break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        total_ms += ms;
-        cudaEventElapsedTime(&ms, g->ev_sweep0, g->ev_sweep1);
-        sweep_ms += ms;
-        cudaEventElapsedTime(&ms, e0, g->ev_sweep0);
-        index_ms += ms;
-        cudaEventElapsedTime(&ms, ep, e1);
-        prune_ms += ms;
-        const StepCounters& C = *g->counters_host;
-        if (C.error) {
-            st = fail(g, (C.error & 4) ? VL_ETIMEOUT : VL_ECUDA,
-                      "vl_translate: device-side error flag " + std::to_string(C.error) +
-                          ((C.error & 4) ? " (a staging barrier wait ran out)" : ""));
-            break;
-        }
-        S.steps++;
-        S.union_blocks = total;
-        S.blocks = (int64_t)C.kept;
-        S.dropped_blocks = (int64_t)C.dropped;
-        S.dropped_mass += C.dropped_mass * g->space.dx[0] * g->space.dx[1] * g->space.dx[2] *
-                          g->vmesh.dv[0] * g->vmesh.dv[1] * g->vmesh.dv[2];
-        S.mass = (C.mass - C.dropped_mass) * g->space.dx[0] * g->space.dx[1] * g->space.dx[2] *
-                 g->vmesh.dv[0] * g->vmesh.dv[1] * g->vmesh.dv[2];
-        g->cur = 1 - g->cur;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(ei);
-    cudaEventDestroy(ep);
-    S.device_ms = total_ms;
-    S.sweep_ms = sweep_ms;
-    S.index_ms = index_ms;
-    S.prune_ms = prune_ms;
+    vl_status st = opts.graph ? translate_graph(g, a, fused, nsteps, opts.capacity, &S)
+                              : translate_steps(g, a, fused, nsteps, &S);
     S.launches = launch_count() - launches0;
     if (S.steps > 0) g->stats = S;
     else g->stats.steps = 0;

@@ -36,6 +36,8 @@ struct LayoutView {
 };
 
 struct GridGeom {
+    const int* abort;  // sticky device flag of a captured step sequence (nullptr: none);
+                       // once set, every later step kernel returns at entry
     int n[3];      // nx, ny, nz
     int W;         // words per row
     int64_t R;     // rows = ny*nz
@@ -236,8 +238,11 @@ struct StepCounters {
     unsigned long long kept;
     unsigned long long dropped;
     unsigned long long work_next;  // persistent-kernel work counter
-    int error;
-    int pad;
+    int error;                     // bit 2: staging wait ran out; bit 3: capacity overflow
+    int done;                      // 1 once every kernel of the step has run
+    long long needed;              // slots the step's union needed (capacity checks)
 };
+
+__device__ __forceinline__ bool aborted(const int* abort) { return abort && *(volatile const int*)abort; }
 
 }  // namespace vlgt

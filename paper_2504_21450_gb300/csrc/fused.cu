@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
     __shared__ int s_nrun;
 
     const GridGeom& G = P.G;
+    if (aborted(G.abort)) return;
     const int tid = threadIdx.x;
     const int v = tid & 15;
     const int hi = tid >> 4;
@@ -477,6 +478,7 @@ __device__ bool row_any(const uint64_t* rowp, int xlo, int xhi)
 __global__ void k_tile_flags(TileArgs T, uint32_t* __restrict__ flags)
 {
     const GridGeom& G = T.G;
+    if (aborted(G.abort)) return;
     int64_t ntiles = (int64_t)T.ntile0 * T.ntile1;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)G.nb * ntiles) return;
@@ -499,8 +501,9 @@ __global__ void k_tile_flags(TileArgs T, uint32_t* __restrict__ flags)
 
 __global__ void k_tile_items(int64_t ntiles, int nb, const uint32_t* __restrict__ flags,
                              const uint32_t* __restrict__ pos, const int64_t* __restrict__ base,
-                             uint32_t* __restrict__ items)
+                             uint32_t* __restrict__ items, const int* abort)
 {
+    if (aborted(abort)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)nb * ntiles) return;
     if (!flags[i]) return;
@@ -529,6 +532,29 @@ vl_status launch_fused(Grid* g, const FusedArgs& P)
 
 }  // namespace
 
+// Work-list buffers of the fused form for this sweep order (allocated before any
+// captured step sequence).
+vl_status fused_worklist_alloc(Grid* g, const StepArgs& a)
+{
+    const GridGeom& G = g->geom;
+    const int ty = a.order[2] == 2 ? 16 : 8;
+    const int64_t ntiles = (int64_t)((G.n[a.order[0]] + TX - 1) / TX) * ((G.n[a.order[1]] + ty - 1) / ty);
+    const int64_t need = ntiles * G.nb;
+    if (need <= g->ntiles_alloc) return VL_OK;
+    g->release(g->tile_flags);
+    g->release(g->tile_pos);
+    g->release(g->items);
+    g->tile_flags = (uint32_t*)g->alloc((size_t)need * 4);
+    g->tile_pos = (uint32_t*)g->alloc((size_t)need * 4);
+    g->items = (uint32_t*)g->alloc((size_t)need * 4);
+    if (!g->tile_flags || !g->tile_pos || !g->items) {
+        g->ntiles_alloc = 0;
+        return fail(g, VL_ENOMEM, "fused form: work-list allocation failed");
+    }
+    g->ntiles_alloc = need;
+    return VL_OK;
+}
+
 vl_status run_fused(Grid* g, const StepArgs& a)
 {
     const GridGeom& G = g->geom;
@@ -542,19 +568,8 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     int64_t ntiles = (int64_t)ntile0 * ntile1;
     if (ntiles > 0xffffffffLL) return fail(g, VL_EINVAL, "fused form: too many tiles");
     int64_t need = ntiles * G.nb;
-    if (need > g->ntiles_alloc) {
-        g->release(g->tile_flags);
-        g->release(g->tile_pos);
-        g->release(g->items);
-        g->tile_flags = (uint32_t*)g->alloc((size_t)need * 4);
-        g->tile_pos = (uint32_t*)g->alloc((size_t)need * 4);
-        g->items = (uint32_t*)g->alloc((size_t)need * 4);
-        if (!g->tile_flags || !g->tile_pos || !g->items) {
-            g->ntiles_alloc = 0;
-            return fail(g, VL_ENOMEM, "fused form: work-list allocation failed");
-        }
-        g->ntiles_alloc = need;
-    }
+    vl_status wst = fused_worklist_alloc(g, a);
+    if (wst != VL_OK) return wst;
     TileArgs T;
     T.G = G;
     T.ubits = B.ubits;
@@ -564,10 +579,10 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     T.ty = ty;
     k_tile_flags<<<nblk(need, 256), 256, 0, g->stream>>>(T, g->tile_flags);
     note_launch();
-    launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, G.nb, g->stream);
-    launch_base_scan(g->item_cnt, g->item_base, G.nb, g->stream);
+    launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, G.nb, g->stream, G.abort);
+    launch_base_scan(g->item_cnt, g->item_base, G.nb, g->stream, G.abort);
     k_tile_items<<<nblk(need, 256), 256, 0, g->stream>>>(ntiles, G.nb, g->tile_flags, g->tile_pos,
-                                                           g->item_base, g->items);
+                                                           g->item_base, g->items, G.abort);
     note_launch();
 
     FusedArgs P;
@@ -586,12 +601,12 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.items = g->items;
     P.item_base = g->item_base;
     P.keepq = B.keepq;
-    P.ctr = g->counters;
-    cudaEventRecord(g->ev_sweep0, g->stream);
+    P.ctr = a.ctr;
+    if (a.time_phases) cudaEventRecord(g->ev_sweep0, g->stream);
     vl_status st;
     if (zuni) st = a.limiter ? launch_fused<16, true, true>(g, P) : launch_fused<16, false, true>(g, P);
     else st = a.limiter ? launch_fused<8, true, false>(g, P) : launch_fused<8, false, false>(g, P);
-    cudaEventRecord(g->ev_sweep1, g->stream);
+    if (a.time_phases) cudaEventRecord(g->ev_sweep1, g->stream);
     return st;
 }
 

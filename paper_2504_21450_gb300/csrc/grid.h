@@ -54,6 +54,14 @@ struct Grid {
     int64_t ntiles_alloc = 0;
     int64_t item_mass_alloc = 0;
     int64_t* host_scalar = nullptr;       // pinned
+    int* abort_flag = nullptr;            // device: sticky abort of a captured step sequence
+    StepCounters* step_ctr = nullptr;     // device [step_ctr_n]: per-step counters (graphs)
+    StepCounters* step_ctr_host = nullptr;  // pinned copy
+    int step_ctr_n = 0;
+    cudaGraphExec_t graph_exec = nullptr; // cached captured step sequence
+    uint64_t graph_key = 0;
+    int64_t graph_kernels = 0;            // kernels in the cached graph
+    cudaStream_t capture_stream = nullptr;
     float4* ctab = nullptr;               // device [2][3][nvmax] sweep constants
     float4* ctab_host = nullptr;          // pinned staging of the same
     double ctab_dt = -1.0;                // dt the table was built for
@@ -79,14 +87,20 @@ vl_status cuda_fail(Grid* g, cudaError_t e, const char* what);
 vl_status layout_alloc_meta(Grid* g, Layout& L);
 void layout_free(Grid* g, Layout& L);
 vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks);
+// Like layout_ensure_pool, but keeps the L.total blocks the pool holds.
+vl_status layout_grow_pool(Grid* g, Layout& L, int64_t blocks);
 // Counts, offsets and dense flags of L from its ubits (woff, cnt, base, dense);
 // returns the total number of slots in *total (synchronises the stream).
 vl_status layout_index(Grid* g, Layout& L, int64_t* total);
 // next.ubits = 27-cell dilation of cur.kbits (periodic).
 void launch_union(Grid* g, const Layout& cur, Layout& next);
+// Device-only part of layout_index (no host synchronisation).
+void launch_index(Grid* g, Layout& L);
 // next.kbits from the per-chunk keep flags; counts kept/dropped blocks and the FP64
-// mass of dropped blocks into g->counters; sets next.dense bit 1 and next.kcnt.
-void launch_pack_keep(Grid* g, Layout& next);
+// mass of dropped blocks into ctr; sets next.dense bit 1 and next.kcnt; marks ctr done.
+void launch_pack_keep(Grid* g, Layout& next, StepCounters* ctr);
+// Sets the abort flag and ctr->error bit 3 when L's slot total exceeds capacity.
+void launch_capacity_check(Grid* g, const Layout& L, int64_t capacity, StepCounters* ctr);
 vl_status set_blocks(Grid* g, int64_t nblocks, const int64_t* off, const uint16_t* ids,
                      const float* vals, int on_device);
 vl_status get_block_count(Grid* g, int64_t* n);
@@ -99,8 +113,9 @@ vl_status moments(Grid* g, double* out, int on_device);
 vl_status total_mass(Grid* g, double* mass);
 // Generic scans used by the layout code and the work lists.
 void launch_seg_scan(const uint32_t* in, uint32_t* out, uint32_t* seg_total, int64_t seg_len,
-                     int64_t nseg, cudaStream_t s);
-void launch_base_scan(const uint32_t* seg_total, int64_t* base, int64_t nseg, cudaStream_t s);
+                     int64_t nseg, cudaStream_t s, const int* abort);
+void launch_base_scan(const uint32_t* seg_total, int64_t* base, int64_t nseg, cudaStream_t s,
+                      const int* abort);
 
 // ---- fused.cu / sweep3.cu --------------------------------------------------
 struct StepArgs {
@@ -111,7 +126,10 @@ struct StepArgs {
     const float4* walk;   // device [3][nvmax]: WalkConst per axis and velocity index
     const float4* sweep;  // device [3][nvmax]: SweepConst per axis and velocity index
     int nvmax;
+    StepCounters* ctr;    // counters of this step
+    bool time_phases;     // record the sweep events (not inside captured graphs)
 };
+vl_status fused_worklist_alloc(Grid* g, const StepArgs& a);
 vl_status run_fused(Grid* g, const StepArgs& a);
 vl_status run_3pass(Grid* g, const StepArgs& a);
 vl_status fused_prepare(Grid* g, const StepArgs& a, int64_t* nwork);

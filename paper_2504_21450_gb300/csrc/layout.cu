@@ -38,8 +38,9 @@ __device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long lon
 
 // Exclusive scan of each segment of seg_len counts; one CTA per segment.
 __global__ void k_seg_scan(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                           uint32_t* __restrict__ seg_total, int64_t seg_len)
+                           uint32_t* __restrict__ seg_total, int64_t seg_len, const int* abort)
 {
+    if (aborted(abort)) return;
     __shared__ uint32_t wsum[32];
     const int64_t seg = blockIdx.x;
     const uint32_t* src = in + seg * seg_len;
@@ -68,8 +69,9 @@ __global__ void k_seg_scan(const uint32_t* __restrict__ in, uint32_t* __restrict
 
 // base[s] = sum of seg_total[0..s), base[nseg] = grand total (64-bit); one CTA.
 __global__ void k_base_scan(const uint32_t* __restrict__ seg_total, int64_t* __restrict__ base,
-                            int64_t nseg)
+                            int64_t nseg, const int* abort)
 {
+    if (aborted(abort)) return;
     __shared__ unsigned long long wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     unsigned long long carry = 0;
@@ -121,6 +123,7 @@ __device__ __forceinline__ uint64_t xdilate(const uint64_t* row, int W, int nx, 
 __global__ void k_union(GridGeom G, const uint64_t* __restrict__ kin, uint64_t* __restrict__ uout,
                         uint32_t* __restrict__ wcount)
 {
+    if (aborted(G.abort)) return;
     int64_t total = (int64_t)G.nb * G.RW;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -147,17 +150,35 @@ __global__ void k_union(GridGeom G, const uint64_t* __restrict__ kin, uint64_t* 
 }
 
 __global__ void k_dense_u(const uint32_t* __restrict__ cnt, uint8_t* __restrict__ dense, int nb,
-                          int64_t N)
+                          int64_t N, const int* abort)
 {
+    if (aborted(abort)) return;
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb) dense[b] = (cnt[b] == (uint32_t)N) ? 1 : 0;
 }
 
 __global__ void k_dense_k(const uint32_t* __restrict__ kcnt, uint8_t* __restrict__ dense, int nb,
-                          int64_t N)
+                          int64_t N, const int* abort, StepCounters* ctr)
 {
+    if (aborted(abort)) return;
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb && kcnt[b] == (uint32_t)N) dense[b] |= 2;
+    if (ctr && b == 0) ctr->done = 1;
+}
+
+// Capacity check of a step whose pools were sized before it ran (captured step
+// sequences): when the union needs more slots than the pools hold, the step and every
+// later one are skipped, leaving the last complete state in its layout.
+__global__ void k_capacity(const int64_t* __restrict__ total, int64_t capacity, int* abort,
+                           StepCounters* ctr)
+{
+    if (aborted(abort)) return;
+    const int64_t t = *total;
+    ctr->needed = (long long)t;
+    if (t > capacity) {
+        ctr->error |= 8;
+        *abort = 1;
+    }
 }
 
 constexpr int kPackThreads = 256;
@@ -169,6 +190,7 @@ __global__ void k_pack_keep(GridGeom G, LayoutView L, const uint8_t* __restrict_
                             uint64_t* __restrict__ kout, uint32_t* __restrict__ kcnt,
                             StepCounters* __restrict__ ctr, int64_t chunks_per_seg)
 {
+    if (aborted(G.abort)) return;
     __shared__ unsigned long long s_kept[kPackThreads / 32], s_drop[kPackThreads / 32];
     __shared__ double s_mass[kPackThreads / 32];
     const int64_t b = blockIdx.x / chunks_per_seg;
@@ -452,16 +474,23 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------------------------
 void launch_seg_scan(const uint32_t* in, uint32_t* out, uint32_t* seg_total, int64_t seg_len,
-                     int64_t nseg, cudaStream_t s)
+                     int64_t nseg, cudaStream_t s, const int* abort)
 {
     if (nseg <= 0) return;
     int threads = seg_len >= 1024 ? kScanThreads : (seg_len >= 256 ? 256 : 64);
-    k_seg_scan<<<(unsigned)nseg, threads, 0, s>>>(in, out, seg_total, seg_len); note_launch();
+    k_seg_scan<<<(unsigned)nseg, threads, 0, s>>>(in, out, seg_total, seg_len, abort); note_launch();
 }
 
-void launch_base_scan(const uint32_t* seg_total, int64_t* base, int64_t nseg, cudaStream_t s)
+void launch_base_scan(const uint32_t* seg_total, int64_t* base, int64_t nseg, cudaStream_t s,
+                      const int* abort)
 {
-    k_base_scan<<<1, kScanThreads, 0, s>>>(seg_total, base, nseg); note_launch();
+    k_base_scan<<<1, kScanThreads, 0, s>>>(seg_total, base, nseg, abort); note_launch();
+}
+
+void launch_capacity_check(Grid* g, const Layout& L, int64_t capacity, StepCounters* ctr)
+{
+    k_capacity<<<1, 1, 0, g->stream>>>(L.base + g->geom.nb, capacity, g->abort_flag, ctr);
+    note_launch();
 }
 
 vl_status layout_alloc_meta(Grid* g, Layout& L)
@@ -516,12 +545,40 @@ vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks)
     return VL_OK;
 }
 
+void launch_index(Grid* g, Layout& L)
+{
+    const GridGeom& G = g->geom;
+    launch_seg_scan(L.wcount, L.woff, L.cnt, G.RW, G.nb, g->stream, G.abort);
+    launch_base_scan(L.cnt, L.base, G.nb, g->stream, G.abort);
+    k_dense_u<<<nblk(G.nb, 256), 256, 0, g->stream>>>(L.cnt, L.dense, G.nb, G.N, G.abort); note_launch();
+}
+
+vl_status layout_grow_pool(Grid* g, Layout& L, int64_t blocks)
+{
+    if (blocks <= L.capacity && L.pool) return VL_OK;
+    float* pool = (float*)g->alloc((size_t)blocks * 64 * sizeof(float));
+    uint8_t* keepq = (uint8_t*)g->alloc((size_t)blocks * 4);
+    if (!pool || !keepq) {
+        g->release(pool);
+        g->release(keepq);
+        return fail(g, VL_ENOMEM, "growing the phase-space pool failed (" + std::to_string(blocks * 256) + " bytes)");
+    }
+    if (L.pool && L.total > 0)
+        cudaMemcpyAsync(pool, L.pool, (size_t)std::min(L.total, L.capacity) * 64 * sizeof(float),
+                        cudaMemcpyDeviceToDevice, g->stream);
+    cudaStreamSynchronize(g->stream);
+    g->release(L.pool);
+    g->release(L.keepq);
+    L.pool = pool;
+    L.keepq = keepq;
+    L.capacity = blocks;
+    return VL_OK;
+}
+
 vl_status layout_index(Grid* g, Layout& L, int64_t* total)
 {
     const GridGeom& G = g->geom;
-    launch_seg_scan(L.wcount, L.woff, L.cnt, G.RW, G.nb, g->stream);
-    launch_base_scan(L.cnt, L.base, G.nb, g->stream);
-    k_dense_u<<<nblk(G.nb, 256), 256, 0, g->stream>>>(L.cnt, L.dense, G.nb, G.N); note_launch();
+    launch_index(g, L);
     cudaMemcpyAsync(g->host_scalar, L.base + G.nb, 8, cudaMemcpyDeviceToHost, g->stream);
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "layout index");
@@ -538,14 +595,15 @@ void launch_union(Grid* g, const Layout& cur, Layout& next)
     k_union<<<blocks, 256, 0, g->stream>>>(G, cur.kbits, next.ubits, next.wcount); note_launch();
 }
 
-void launch_pack_keep(Grid* g, Layout& next)
+void launch_pack_keep(Grid* g, Layout& next, StepCounters* ctr)
 {
     const GridGeom& G = g->geom;
     int64_t cps = (G.RW + kPackThreads - 1) / kPackThreads;
     cudaMemsetAsync(next.kcnt, 0, (size_t)G.nb * 4, g->stream);
     k_pack_keep<<<(unsigned)(cps * G.nb), kPackThreads, 0, g->stream>>>(
-        G, next.view(), next.keepq, next.kbits, next.kcnt, g->counters, cps); note_launch();
-    k_dense_k<<<nblk(G.nb, 256), 256, 0, g->stream>>>(next.kcnt, next.dense, G.nb, G.N); note_launch();
+        G, next.view(), next.keepq, next.kbits, next.kcnt, ctr, cps); note_launch();
+    k_dense_k<<<nblk(G.nb, 256), 256, 0, g->stream>>>(next.kcnt, next.dense, G.nb, G.N, G.abort, ctr);
+    note_launch();
 }
 
 namespace {
@@ -616,7 +674,7 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     vl_status st = layout_index(g, L, &total);
     if (st != VL_OK) return st;
     if (total != M) return fail(g, VL_EINVAL, "vl_set_blocks: duplicate block ids");
-    k_dense_k<<<nblk(G.nb, 256), 256, 0, s>>>(L.cnt, L.dense, G.nb, G.N); note_launch();
+    k_dense_k<<<nblk(G.nb, 256), 256, 0, s>>>(L.cnt, L.dense, G.nb, G.N, nullptr, nullptr); note_launch();
     st = layout_ensure_pool(g, L, std::max<int64_t>(M, 1));
     if (st != VL_OK) return st;
     if (M > 0) { k_scatter<<<nblk(M * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, vals, M); note_launch(); }
@@ -664,8 +722,8 @@ vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capaci
     if (!ccnt || !cexc || !ctot || !cbase) return fail(g, VL_ENOMEM, "block listing: scratch allocation failed");
     cudaMemsetAsync(ccnt, 0, (size_t)nchunk * chunk * 4, s);
     k_cell_counts<<<nblk(Wn.ncell, 256), 256, 0, s>>>(G, Wn, L.kbits, ccnt); note_launch();
-    launch_seg_scan(ccnt, cexc, ctot, chunk, nchunk, s);
-    launch_base_scan(ctot, cbase, nchunk, s);
+    launch_seg_scan(ccnt, cexc, ctot, chunk, nchunk, s, nullptr);
+    launch_base_scan(ctot, cbase, nchunk, s, nullptr);
     cudaMemcpyAsync(g->host_scalar, cbase + nchunk, 8, cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "block listing");

@@ -123,6 +123,8 @@ __global__ void k_noalloc_setup(SetupArgs A)
         A.ctr->dropped = 0;
         A.ctr->work_next = 0;
         A.ctr->error = 0;
+        A.ctr->done = 0;
+        A.ctr->needed = 0;
     }
 }
 
@@ -161,6 +163,7 @@ extern "C" vl_status vl_translate_dense_noalloc(const vl_space_desc* space,
         if ((lo > hi ? lo : hi) * dt / space->dx[d] > 1.0) return VL_ECFL;
     }
     GridGeom G;
+    G.abort = nullptr;
     for (int d = 0; d < 3; d++) G.n[d] = space->n[d];
     G.W = (space->n[0] + 63) / 64;
     G.R = (int64_t)space->n[1] * space->n[2];

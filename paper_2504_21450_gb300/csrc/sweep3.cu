@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     __shared__ int s_rout[kPencils][kMaxLine];
     __shared__ int s_any[kPencils];
     const GridGeom& G = P.G;
+    if (aborted(G.abort)) return;
     const int b = (int)(blockIdx.x / P.groups);
     const int64_t grp = blockIdx.x % P.groups;
     const int nd = G.n[P.dim];
@@ -181,7 +182,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
     for (int d = 0; d < 3; d++)
         if (G.n[d] > kMaxLine)
             return fail(g, VL_EINVAL, "3-pass form: grid extent above 1024 cells");
-    cudaEventRecord(g->ev_sweep0, g->stream);
+    if (a.time_phases) cudaEventRecord(g->ev_sweep0, g->stream);
     for (int j = 0; j < 3; j++) {
         int d = a.order[j];
         PassArgs P;
@@ -196,7 +197,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         P.last = j == 2 ? 1 : 0;
         P.thr = (float)g->threshold;
         P.keepq = B.keepq;
-        P.ctr = g->counters;
+        P.ctr = a.ctr;
         int64_t npen = G.N / G.n[d];
         P.groups = (npen + kPencils - 1) / kPencils;
         int64_t nblocks = P.groups * G.nb;
@@ -208,7 +209,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
             k_pass<false><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P); note_launch();
         }
     }
-    cudaEventRecord(g->ev_sweep1, g->stream);
+    if (a.time_phases) cudaEventRecord(g->ev_sweep1, g->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(g, e, "3-pass sweep launch");
     return VL_OK;

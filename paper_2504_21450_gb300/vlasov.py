@@ -41,7 +41,8 @@ class vl_device(ctypes.Structure):
 
 class vl_translate_opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("limiter", ctypes.c_int), ("ghost", ctypes.c_int),
-                ("tile", ctypes.c_int * 2), ("check", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("tile", ctypes.c_int * 2), ("check", ctypes.c_int), ("graph", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("capacity", ctypes.c_int64), ("reserved", ctypes.c_int * 4)]
 
 
 class vl_step_stats(ctypes.Structure):
@@ -50,7 +51,9 @@ class vl_step_stats(ctypes.Structure):
                 ("mass", ctypes.c_double), ("dropped_mass", ctypes.c_double),
                 ("mass_before", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("sweep_ms", ctypes.c_double), ("index_ms", ctypes.c_double),
-                ("prune_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("prune_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("capacity_regrows", ctypes.c_int64),
+                ("capacity", ctypes.c_int64)]
 
 
 class VlError(RuntimeError):
@@ -291,11 +294,13 @@ class Grid:
         return off, ids[:m], vals[:m]
 
     def translate(self, dt: float, order: str = "xyz", nsteps: int = 1, form: int = VL_FORM_FUSED,
-                  limiter: bool = True, check: bool = False):
+                  limiter: bool = True, check: bool = False, graph: bool = False, capacity: int = 0):
         o = vl_translate_opts_default()
         o.form = int(form)
         o.limiter = int(bool(limiter))
         o.check = int(bool(check))
+        o.graph = int(bool(graph))
+        o.capacity = int(capacity)
         vl_translate(self.handle, dt, order, nsteps, o)
 
     def moments(self) -> np.ndarray:
