@@ -63,7 +63,11 @@ typedef enum {
 typedef enum {
     VL_FORM_FUSED = 0,  /* Ghost Translation: one tile+halo load, x->y->z in one kernel */
     VL_FORM_3PASS = 1,  /* classical: one HBM round trip per sweep direction */
-    VL_FORM_AUTO = 2    /* pick per workload (autotuner cache) */
+    VL_FORM_AUTO = 2    /* pick per workload: the first steps of the first call for a
+                           workload probe each form (they compute the same result) and
+                           the fastest is cached per workload key for later calls; with
+                           the environment variable VLGT_TUNE_CACHE naming a file the
+                           choices also persist across processes (JSON lines) */
 } vl_form;
 
 /* Spatial box: n cells per dimension, cell size dx, origin x0 (periodic). */
@@ -131,6 +135,10 @@ typedef struct {
     int64_t graph_replays;  /* graph mode: captured sequences launched (incl. re-runs) */
     int64_t capacity_regrows; /* graph mode: capacity overflows recovered from */
     int64_t capacity;       /* graph mode: blocks per layout at the end of the call */
+    int form_used;          /* vl_form of the last step (after autotuning) */
+    int tile_rows_used;     /* fused form: tile rows along the second sweep axis */
+    double tune_ms[3];      /* autotuner probes (ms per step): fused 16-row tile, fused
+                               8-row tile, 3-pass; 0 = not probed in this call */
 } vl_step_stats;
 
 void vl_translate_opts_default(vl_translate_opts* opts);
@@ -180,6 +188,17 @@ vl_status vl_get_blocks_window(vl_grid* grid, const int origin[3], const int siz
  * Errors: VL_ECFL (Section 2.1's one-neighbour limit), VL_EINVAL, VL_ENOMEM, VL_ECUDA. */
 vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                        const vl_translate_opts* opts);
+
+/* Checkpoint (the paper restarts its runs from a saved state, Section 4.2): the grid's
+ * state as one self-describing host buffer -- a header (magic "VLGT", format version,
+ * spatial extents, velocity mesh, cell and velocity sizes, threshold, block count)
+ * followed by the per-cell lists (cell_offsets, block_ids, values) of vl_get_blocks.
+ * vl_export with buf == NULL stores the required size in *size; otherwise *size must
+ * hold the buffer's size (VL_ECAPACITY when too small) and receives the bytes written.
+ * vl_import replaces the state of a grid with the same extents and velocity mesh
+ * (VL_EINVAL otherwise, or for a damaged buffer). */
+vl_status vl_export(vl_grid* grid, void* buf, size_t* size);
+vl_status vl_import(vl_grid* grid, const void* buf, size_t size);
 
 /* Velocity moments per cell (particle mass 1), FP64: out[c*7 + k] for
  * k = n, nVx, nVy, nVz, Pxx, Pyy, Pzz with n = sum f dv^3, nV_d = sum v_d f dv^3,

@@ -534,10 +534,14 @@ vl_status launch_fused(Grid* g, const FusedArgs& P)
 
 // Work-list buffers of the fused form for this sweep order (allocated before any
 // captured step sequence).
+// Tile rows along the second sweep axis: 16 when the streamed axis is the velocity
+// chunk's own axis (unless 8 is asked for), 8 otherwise.
+int tile_rows(const StepArgs& a) { return (a.order[2] == 2 && a.tile[1] != 8) ? 16 : 8; }
+
 vl_status fused_worklist_alloc(Grid* g, const StepArgs& a)
 {
     const GridGeom& G = g->geom;
-    const int ty = a.order[2] == 2 ? 16 : 8;
+    const int ty = tile_rows(a);
     const int64_t ntiles = (int64_t)((G.n[a.order[0]] + TX - 1) / TX) * ((G.n[a.order[1]] + ty - 1) / ty);
     const int64_t need = ntiles * G.nb;
     if (need <= g->ntiles_alloc) return VL_OK;
@@ -562,7 +566,7 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     Layout& B = g->lay[1 - g->cur];
     int ax[3] = {a.order[0], a.order[1], a.order[2]};
     const bool zuni = ax[2] == 2;  // the streamed axis is the chunk's (vz) axis
-    const int ty = zuni ? 16 : 8;
+    const int ty = tile_rows(a);
     int ntile0 = (G.n[ax[0]] + TX - 1) / TX;
     int ntile1 = (G.n[ax[1]] + ty - 1) / ty;
     int64_t ntiles = (int64_t)ntile0 * ntile1;
@@ -604,8 +608,12 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.ctr = a.ctr;
     if (a.time_phases) cudaEventRecord(g->ev_sweep0, g->stream);
     vl_status st;
-    if (zuni) st = a.limiter ? launch_fused<16, true, true>(g, P) : launch_fused<16, false, true>(g, P);
-    else st = a.limiter ? launch_fused<8, true, false>(g, P) : launch_fused<8, false, false>(g, P);
+    if (zuni && ty == 16)
+        st = a.limiter ? launch_fused<16, true, true>(g, P) : launch_fused<16, false, true>(g, P);
+    else if (zuni)
+        st = a.limiter ? launch_fused<8, true, true>(g, P) : launch_fused<8, false, true>(g, P);
+    else
+        st = a.limiter ? launch_fused<8, true, false>(g, P) : launch_fused<8, false, false>(g, P);
     if (a.time_phases) cudaEventRecord(g->ev_sweep1, g->stream);
     return st;
 }

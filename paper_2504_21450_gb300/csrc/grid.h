@@ -130,6 +130,7 @@ struct StepArgs {
     bool time_phases;     // record the sweep events (not inside captured graphs)
 };
 vl_status fused_worklist_alloc(Grid* g, const StepArgs& a);
+int tile_rows(const StepArgs& a);
 vl_status run_fused(Grid* g, const StepArgs& a);
 vl_status run_3pass(Grid* g, const StepArgs& a);
 vl_status fused_prepare(Grid* g, const StepArgs& a, int64_t* nwork);

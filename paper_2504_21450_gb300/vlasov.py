@@ -53,7 +53,8 @@ class vl_step_stats(ctypes.Structure):
                 ("sweep_ms", ctypes.c_double), ("index_ms", ctypes.c_double),
                 ("prune_ms", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("graph_replays", ctypes.c_int64), ("capacity_regrows", ctypes.c_int64),
-                ("capacity", ctypes.c_int64)]
+                ("capacity", ctypes.c_int64), ("form_used", ctypes.c_int),
+                ("tile_rows_used", ctypes.c_int), ("tune_ms", ctypes.c_double * 3)]
 
 
 class VlError(RuntimeError):
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "vl_mass": (i, [p, p]),
         "vl_stats": (i, [p, p]),
         "vl_translate_dense_noalloc": (i, [p, p, d, ctypes.c_char_p, i, p, p, p, p]),
+        "vl_export": (i, [p, p, p]),
+        "vl_import": (i, [p, p, ctypes.c_size_t]),
         "vl_status_str": (ctypes.c_char_p, [i]),
         "vl_last_error": (ctypes.c_char_p, [p]),
     }
@@ -293,9 +296,22 @@ class Grid:
                              vals.ctypes.data, 0)
         return off, ids[:m], vals[:m]
 
+    def export(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(load().vl_export(self.handle, None, ctypes.byref(n)), "vl_export", self.handle)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(load().vl_export(self.handle, buf, ctypes.byref(n)), "vl_export", self.handle)
+        return buf.raw[: n.value]
+
+    def import_(self, data: bytes) -> None:
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(load().vl_import(self.handle, buf, len(data)), "vl_import", self.handle)
+
     def translate(self, dt: float, order: str = "xyz", nsteps: int = 1, form: int = VL_FORM_FUSED,
-                  limiter: bool = True, check: bool = False, graph: bool = False, capacity: int = 0):
+                  limiter: bool = True, check: bool = False, graph: bool = False, capacity: int = 0,
+                  tile_rows: int = 0):
         o = vl_translate_opts_default()
+        o.tile[1] = int(tile_rows)
         o.form = int(form)
         o.limiter = int(bool(limiter))
         o.check = int(bool(check))

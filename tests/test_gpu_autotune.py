@@ -1,0 +1,84 @@
+"""The form/tile autotuner: probes the fused Ghost Translation kernel with 16- and 8-row
+tiles and the classical 3-pass form on the first steps of a workload (Section 3's
+trade-off measured per workload) and keeps the fastest."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_21450_gb300 import inputs, vlasov
+
+from parity import gpu_grid
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    vlasov.load(build_if_missing=True)
+
+
+def case():
+    n = (40, 33, 18)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.3, seed=70)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0, -3.0, -4.5), dv=(1.0,) * 3)
+    return init, mesh
+
+
+def run(mesh, init, nsteps, form, tile_rows=0):
+    g = gpu_grid(mesh, 0.1)
+    g.set_blocks(init.off, init.ids, init.vals)
+    g.translate(0.2, "xyz", nsteps, form, check=True, tile_rows=tile_rows)
+    s = g.stats()
+    out = g.get_blocks()
+    g.close()
+    return out, s
+
+
+def test_eight_row_tiles_give_the_same_state():
+    init, mesh = case()
+    a, _ = run(mesh, init, 3, vlasov.VL_FORM_FUSED)
+    b, sb = run(mesh, init, 3, vlasov.VL_FORM_FUSED, tile_rows=8)
+    assert sb.tile_rows_used == 8
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_autotuned_run_equals_fixed_form():
+    init, mesh = case()
+    ref, _ = run(mesh, init, 8, vlasov.VL_FORM_FUSED)
+    got, s = run(mesh, init, 8, vlasov.VL_FORM_AUTO)
+    for x, y in zip(ref, got):
+        np.testing.assert_array_equal(x, y)
+    assert s.steps == 8
+    assert s.form_used in (vlasov.VL_FORM_FUSED, vlasov.VL_FORM_3PASS)
+    assert all(t > 0 for t in s.tune_ms)  # all three candidates probed (order ends in z)
+    best = int(np.argmin(list(s.tune_ms)))
+    assert s.form_used == (vlasov.VL_FORM_3PASS if best == 2 else vlasov.VL_FORM_FUSED)
+
+
+def test_tuning_cache_persists(tmp_path):
+    cache = tmp_path / "tune.jsonl"
+    code = (
+        "import sys; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from test_gpu_autotune import case, run\n"
+        "from paper_2504_21450_gb300 import vlasov\n"
+        "init, mesh = case()\n"
+        "_, s = run(mesh, init, 6, vlasov.VL_FORM_AUTO)\n"
+        "print(s.form_used, s.tile_rows_used)\n" % (ROOT, os.path.join(ROOT, "tests")))
+    env = dict(os.environ, VLGT_TUNE_CACHE=str(cache))
+    first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert first.returncode == 0, first.stderr
+    rec = [json.loads(line) for line in cache.read_text().splitlines()]
+    assert len(rec) == 1 and rec[0]["form"] in (0, 1) and len(rec[0]["ms"]) == 3
+    second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert second.returncode == 0, second.stderr
+    assert len(cache.read_text().splitlines()) == 1  # reused, not re-tuned
+    assert second.stdout.split() == first.stdout.split()

@@ -215,3 +215,27 @@ def test_uniform_config_full_size_window(form):
                                         post, thr, cfg.dt, "xyz", cells=inner)
     assert err <= VAL_TOL * fmax, (err, fmax)
     g.close()
+
+
+def test_checkpoint_roundtrip_and_restart():
+    """Export mid-run, import into a fresh grid, continue: same state as an
+    uninterrupted run (restart from a checkpoint, Section 4.2)."""
+    n = (20, 12, 9)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.3, seed=47)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    a = gpu_grid(mesh, 0.2)
+    a.set_blocks(init.off, init.ids, init.vals)
+    a.translate(0.2, "xyz", 2, check=True)
+    blob = a.export()
+    a.translate(0.2, "xyz", 3, check=True)
+    b = gpu_grid(mesh, 0.2)
+    b.import_(blob)
+    b.translate(0.2, "xyz", 3, check=True)
+    for x, y in zip(a.get_blocks(), b.get_blocks()):
+        np.testing.assert_array_equal(x, y)
+    other = gpu_grid(oracle.Mesh(n=(20, 12, 8), nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3), 0.2)
+    with pytest.raises(vlasov.VlError) as e:
+        other.import_(blob)
+    assert e.value.status == vlasov.VL_EINVAL
+    with pytest.raises(vlasov.VlError):
+        b.import_(blob[:100])
