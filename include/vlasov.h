@@ -139,6 +139,8 @@ typedef struct {
     int tile_rows_used;     /* fused form: tile rows along the second sweep axis */
     double tune_ms[3];      /* autotuner probes (ms per step): fused 16-row tile, fused
                                8-row tile, 3-pass; 0 = not probed in this call */
+    int64_t updates;        /* phase-space cell updates of the call: velocity cells present
+                               at the start of each step, summed over its steps */
 } vl_step_stats;
 
 void vl_translate_opts_default(vl_translate_opts* opts);

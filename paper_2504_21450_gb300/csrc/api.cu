@@ -96,10 +96,12 @@ double phase_volume(const Grid* g)
            g->vmesh.dv[2];
 }
 
-void add_step(const Grid* g, const StepCounters& C, vl_step_stats* S)
+void add_step(Grid* g, const StepCounters& C, vl_step_stats* S)
 {
     const double vol = phase_volume(g);
     S->steps++;
+    S->updates += g->present * 64;
+    g->present = (int64_t)C.kept;
     S->union_blocks = (int64_t)C.needed;
     S->blocks = (int64_t)C.kept;
     S->dropped_blocks = (int64_t)C.dropped;
@@ -116,7 +118,6 @@ vl_status enqueue_step(Grid* g, StepArgs a, bool fused, bool graph, int64_t capa
     Layout& A = g->lay[g->cur];
     Layout& B = g->lay[1 - g->cur];
     a.ctr = ctr;
-    a.time_phases = !graph;
     cudaMemsetAsync(ctr, 0, sizeof(StepCounters), g->stream);
     launch_union(g, A, B);
     if (graph) {
@@ -146,8 +147,10 @@ vl_status step_error(Grid* g, const StepCounters& C)
 }
 
 // Step by step, with the counters read back after every step.
-vl_status translate_steps(Grid* g, const StepArgs& a, bool fused, int nsteps, vl_step_stats* S)
+vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_stats* S)
 {
+    a.ev0 = g->ev_sweep0;
+    a.ev1 = g->ev_sweep1;
     cudaEvent_t e0, e1, ep;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -232,6 +235,12 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
             if (!g->step_ctr || e != cudaSuccess) st = fail(g, VL_ENOMEM, "graph mode: counter allocation failed");
             else g->step_ctr_n = n;
         }
+        while (st == VL_OK && (int)g->graph_ev.size() < 2 * n) {
+            cudaEvent_t ev = nullptr;
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) st = cuda_fail(g, e, "graph mode: events");
+            else g->graph_ev.push_back(ev);
+        }
         if (st != VL_OK) break;
         uint64_t key = 0;
         const uint64_t parts[] = {(uint64_t)n, (uint64_t)fused, (uint64_t)a.limiter, (uint64_t)a.order[0],
@@ -255,7 +264,12 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
             if (e != cudaSuccess) st = cuda_fail(g, e, "graph mode: begin capture");
             if (st == VL_OK) cudaMemsetAsync(g->abort_flag, 0, sizeof(int), g->stream);
             for (int k = 0; k < n && st == VL_OK; k++) {
-                st = enqueue_step(g, a, fused, true, cap, g->step_ctr + k);
+                // event record nodes around each step's sweep kernels (sweep time per step)
+                StepArgs ak = a;
+                ak.ev0 = g->graph_ev[2 * k];
+                ak.ev1 = g->graph_ev[2 * k + 1];
+                ak.ev_node = true;
+                st = enqueue_step(g, ak, fused, true, cap, g->step_ctr + k);
                 g->cur = 1 - g->cur;
             }
             cudaGraph_t graph = nullptr;
@@ -292,6 +306,10 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
         int d = 0;
         while (d < n && g->step_ctr_host[d].done) {
             add_step(g, g->step_ctr_host[d], S);
+            if (cudaEventElapsedTime(&ms, g->graph_ev[2 * d], g->graph_ev[2 * d + 1]) == cudaSuccess)
+                S->sweep_ms += ms;
+            else
+                cudaGetLastError();  // timing unavailable; leave no error behind
             d++;
         }
         if (d > 0) {
@@ -521,6 +539,7 @@ vl_status vl_grid_destroy(vl_grid* grid)
     if (g->step_ctr_host) cudaFreeHost(g->step_ctr_host);
     if (g->ev_sweep0) cudaEventDestroy(g->ev_sweep0);
     if (g->ev_sweep1) cudaEventDestroy(g->ev_sweep1);
+    for (cudaEvent_t ev : g->graph_ev) cudaEventDestroy(ev);
     g->release(g->ctab);
     if (g->ctab_host) cudaFreeHost(g->ctab_host);
     if (g->counters_host) cudaFreeHost(g->counters_host);
@@ -536,7 +555,10 @@ vl_status vl_set_blocks(vl_grid* grid, int64_t nblocks, const int64_t* cell_offs
     Grid* g = reinterpret_cast<Grid*>(grid);
     DeviceGuard dg(g->dev.device);
     vl_status st = set_blocks(g, nblocks, cell_offsets, block_ids, values, on_device);
-    if (st == VL_OK) g->stats.mass = NAN;
+    if (st == VL_OK) {
+        g->stats.mass = NAN;
+        g->present = nblocks;
+    }
     return st;
 }
 
@@ -654,7 +676,10 @@ vl_status vl_import(vl_grid* grid, const void* buf, size_t size)
     p += (size_t)M * 256;
     const uint16_t* ids = reinterpret_cast<const uint16_t*>(p);
     vl_status st = set_blocks(g, M, off, ids, vals, 0);
-    if (st == VL_OK) g->stats.mass = NAN;
+    if (st == VL_OK) {
+        g->stats.mass = NAN;
+        g->present = M;
+    }
     return st;
 }
 
@@ -785,6 +810,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                 S.dropped_blocks = probe.dropped_blocks;
                 S.dropped_mass += probe.dropped_mass;
                 S.mass = probe.mass;
+                S.updates += probe.updates;
                 done += 2;
                 entry.ms[c] = probe.device_ms;
                 if (probe.device_ms < best) {

@@ -109,6 +109,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_add_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Number of consecutive cells from x on (at most maxlen) set in both row bitmaps k and u.
+__device__ __forceinline__ int run_of_ones(const uint64_t* k, const uint64_t* u, int x, int maxlen)
+{
+    int n = 0;
+    while (n < maxlen) {
+        const int xx = x + n;
+        const uint64_t w = (k[xx >> 6] & u[xx >> 6]) >> (xx & 63);
+        const int avail = 64 - (xx & 63);
+        const int ones = (~w == 0ull) ? 64 : __ffsll((long long)~w) - 1;
+        n += min(ones, avail);
+        if (ones < avail) break;
+    }
+    return min(n, maxlen);
+}
 // 1D bulk copy global -> shared (TMA), completion counted on an mbarrier
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
 {
@@ -194,13 +217,14 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         const bool dense_in = (P.in.dense[b] & 3) == 3;
         const bool dense_out = (P.out.dense[b] & 1) != 0;
         const bool bulk = dense_in && a0 == 0;  // halo rows are contiguous runs in HBM
+        const bool sbulk = !dense_in && a0 == 0;  // sparse rows: runs of present cells
         const bool full = e0 == TX && e1 == TY;
         const int64_t ibase = ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * NV;
         const int64_t obase = ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * NV;
         const int64_t okeep = (int64_t)P.out.base[b];
 
         // contiguous runs of a halo row along axis 0 (split at the periodic wrap)
-        if (tid == 0 && bulk) {
+        if (tid == 0 && (bulk || sbulk)) {
             int u0 = 0, nr = 0;
             while (u0 < EX) {
                 const int x = wrapi(t0 - H + u0, n0);
@@ -271,6 +295,54 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                             bulk_g2s(dst + s_run[k][0] * NV, src + s_run[k][1] * NV,
                                      (unsigned)(s_run[k][2] * NV * 4), bar);
                     }
+                } else if (sbulk) {
+                    // lane u1 stages halo row u1: one bulk copy per run of present cells
+                    // (consecutive slots), zeros for absent ones; every lane adds its bytes
+                    // to the barrier's expected count before one lane arrives
+                    uint64_t* bar = &s_bar[(gstep + s) % NST];
+                    if (ltid < EY) {
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        const int64_t row = (int64_t)pr1[ltid] + r2;
+                        const uint64_t* krow = P.in.kbits + (int64_t)b * G.RW + row * G.W;
+                        const uint64_t* urow = P.in.ubits + (int64_t)b * G.RW + row * G.W;
+                        const uint32_t* wrow = P.in.woff + (int64_t)b * G.RW + row * G.W;
+                        float* dst = st + ltid * SROW;
+                        unsigned bytes = 0;
+                        for (int pass = 0; pass < 2; pass++) {
+                            for (int k = 0; k < s_nrun; k++) {
+                                const int u0 = s_run[k][0], x0 = s_run[k][1], len = s_run[k][2];
+                                int u = 0;
+                                while (u < len) {
+                                    const int x = x0 + u;
+                                    if (!(((krow[x >> 6] & urow[x >> 6]) >> (x & 63)) & 1ull)) {
+                                        if (pass == 1) {
+                                            float4* z = reinterpret_cast<float4*>(dst + (u0 + u) * NV);
+                                            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+                                            z[0] = zero;
+                                            z[1] = zero;
+                                            z[2] = zero;
+                                            z[3] = zero;
+                                        }
+                                        u++;
+                                        continue;
+                                    }
+                                    const int rl = run_of_ones(krow, urow, x, len - u);
+                                    if (pass == 0) {
+                                        bytes += (unsigned)(rl * NV * 4);
+                                    } else {
+                                        const int64_t r = (int64_t)wrow[x >> 6] +
+                                                          __popcll(urow[x >> 6] & ((1ull << (x & 63)) - 1ull));
+                                        bulk_g2s(dst + (u0 + u) * NV, P.in.pool + ibase + r * NV,
+                                                 (unsigned)(rl * NV * 4), bar);
+                                    }
+                                    u += rl;
+                                }
+                            }
+                            if (pass == 0) mbar_add_tx(bar, bytes);
+                        }
+                    }
+                    __syncwarp();
+                    if (ltid == 0) mbar_arrive(bar);
                 } else {
                     for (int k = ltid; k < EX * EY * 4; k += NLD) {
                         int cell = k >> 2, piece = k & 3;
@@ -286,7 +358,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             cp_async_commit();
         };
         auto wait_plane = [&](int s) {
-            if (bulk) {
+            if (bulk || sbulk) {
                 uint64_t* bar = &s_bar[(gstep + s) % NST];
                 const unsigned parity = ((gstep + s) / NST) & 1u;
                 unsigned polls = 0;
@@ -446,7 +518,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         __syncthreads();
         if (loader) keep_flags(nsteps - 1);
         cp_async_wait<0>();
-        if (bulk) gstep += (unsigned)nsteps;
+        if (bulk || sbulk) gstep += (unsigned)nsteps;
         double m = (double)msum;
         for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
         if (lane == 0 && m != 0.0) atomicAdd(&P.ctr->mass, m);
@@ -606,7 +678,7 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.item_base = g->item_base;
     P.keepq = B.keepq;
     P.ctr = a.ctr;
-    if (a.time_phases) cudaEventRecord(g->ev_sweep0, g->stream);
+    record_sweep_event(a.ev0, g->stream, a.ev_node);
     vl_status st;
     if (zuni && ty == 16)
         st = a.limiter ? launch_fused<16, true, true>(g, P) : launch_fused<16, false, true>(g, P);
@@ -614,7 +686,7 @@ vl_status run_fused(Grid* g, const StepArgs& a)
         st = a.limiter ? launch_fused<8, true, true>(g, P) : launch_fused<8, false, true>(g, P);
     else
         st = a.limiter ? launch_fused<8, true, false>(g, P) : launch_fused<8, false, false>(g, P);
-    if (a.time_phases) cudaEventRecord(g->ev_sweep1, g->stream);
+    record_sweep_event(a.ev1, g->stream, a.ev_node);
     return st;
 }
 

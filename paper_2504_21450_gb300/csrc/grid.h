@@ -2,6 +2,8 @@
 // translation units of libvlgt (internal; the public interface is include/vlasov.h).
 #pragma once
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 #include <algorithm>
@@ -41,6 +43,7 @@ struct Grid {
     Layout lay[2];   // lay[cur] holds the state, lay[1-cur] the next step's
     int cur = 0;
     bool has_state = false;
+    int64_t present = 0;  // blocks present in the current state (host copy)
 
     // scratch
     StepCounters* counters = nullptr;     // device
@@ -69,6 +72,7 @@ struct Grid {
     vl_step_stats stats{};
     int64_t launches = 0;                 // kernels launched by the library (running count)
     cudaEvent_t ev_sweep0 = nullptr, ev_sweep1 = nullptr;  // bracket the sweep kernels
+    std::vector<cudaEvent_t> graph_ev;  // per captured step: sweep start, sweep end
     std::string last_error;
 
     void* alloc(size_t bytes);
@@ -127,8 +131,17 @@ struct StepArgs {
     const float4* sweep;  // device [3][nvmax]: SweepConst per axis and velocity index
     int nvmax;
     StepCounters* ctr;    // counters of this step
-    bool time_phases;     // record the sweep events (not inside captured graphs)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the sweep kernels when set
+    bool ev_node = false;  // inside a stream capture: record as event record nodes
 };
+// Records ev on s; inside a capture as an event record node, which the graph records on
+// every replay (a plain record there would only mark a capture dependency).
+inline void record_sweep_event(cudaEvent_t ev, cudaStream_t s, bool node)
+{
+    if (!ev) return;
+    if (node) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else cudaEventRecord(ev, s);
+}
 vl_status fused_worklist_alloc(Grid* g, const StepArgs& a);
 int tile_rows(const StepArgs& a);
 vl_status run_fused(Grid* g, const StepArgs& a);

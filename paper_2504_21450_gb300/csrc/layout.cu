@@ -299,11 +299,11 @@ __global__ void k_mark(GridGeom G, const int64_t* __restrict__ off, const uint16
 
 __global__ void k_scatter(GridGeom G, LayoutView L, const uint16_t* __restrict__ ids,
                           const int64_t* __restrict__ cell_of, const float* __restrict__ vals,
-                          int64_t M)
+                          int64_t t0, int64_t M)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M * 64) return;
-    int64_t t = i >> 6;
+    int64_t t = t0 + (i >> 6);  // block index in the full list; vals holds blocks t0 ..
     int v = (int)(i & 63);
     int b = ids[t];
     int64_t c = cell_of[t];
@@ -531,7 +531,7 @@ void layout_free(Grid* g, Layout& L)
 vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks)
 {
     if (blocks <= L.capacity && L.pool) return VL_OK;
-    int64_t cap = blocks + blocks / 8 + 64;
+    int64_t cap = blocks + blocks / 32 + 64;
     g->release(L.pool);
     g->release(L.keepq);
     L.pool = (float*)g->alloc((size_t)cap * 64 * sizeof(float));
@@ -637,20 +637,15 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     Scratch sc(g);
     const int64_t* off = off_in;
     const uint16_t* ids = ids_in;
-    const float* vals = vals_in;
+    const float* vals = on_device ? vals_in : nullptr;  // host values are streamed below
     if (!on_device) {
         int64_t* d_off = (int64_t*)sc.get((size_t)(G.N + 1) * 8);
         uint16_t* d_ids = (uint16_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 2);
-        float* d_vals = (float*)sc.get((size_t)std::max<int64_t>(M, 1) * 256);
-        if (!d_off || !d_ids || !d_vals) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
+        if (!d_off || !d_ids) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
         cudaMemcpyAsync(d_off, off_in, (size_t)(G.N + 1) * 8, cudaMemcpyHostToDevice, s);
-        if (M > 0) {
-            cudaMemcpyAsync(d_ids, ids_in, (size_t)M * 2, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(d_vals, vals_in, (size_t)M * 256, cudaMemcpyHostToDevice, s);
-        }
+        if (M > 0) cudaMemcpyAsync(d_ids, ids_in, (size_t)M * 2, cudaMemcpyHostToDevice, s);
         off = d_off;
         ids = d_ids;
-        vals = d_vals;
     }
     Layout& L = g->lay[g->cur];
     size_t words = (size_t)G.nb * (size_t)G.RW;
@@ -677,7 +672,22 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     k_dense_k<<<nblk(G.nb, 256), 256, 0, s>>>(L.cnt, L.dense, G.nb, G.N, nullptr, nullptr); note_launch();
     st = layout_ensure_pool(g, L, std::max<int64_t>(M, 1));
     if (st != VL_OK) return st;
-    if (M > 0) { k_scatter<<<nblk(M * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, vals, M); note_launch(); }
+    if (M > 0 && on_device) {
+        k_scatter<<<nblk(M * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, vals, 0, M);
+        note_launch();
+    } else if (M > 0) {
+        // host values: copied and scattered in chunks, so the device never holds a second
+        // full copy of the state
+        const int64_t chunk = std::min<int64_t>(M, (int64_t)1 << 22);  // 1 GiB of values
+        float* stage_buf = (float*)sc.get((size_t)chunk * 256);
+        if (!stage_buf) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
+        for (int64_t t0 = 0; t0 < M; t0 += chunk) {
+            const int64_t m = std::min(chunk, M - t0);
+            cudaMemcpyAsync(stage_buf, vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice, s);
+            k_scatter<<<nblk(m * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, stage_buf, t0, m);
+            note_launch();
+        }
+    }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks scatter");
     g->has_state = true;

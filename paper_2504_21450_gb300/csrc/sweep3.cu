@@ -182,7 +182,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
     for (int d = 0; d < 3; d++)
         if (G.n[d] > kMaxLine)
             return fail(g, VL_EINVAL, "3-pass form: grid extent above 1024 cells");
-    if (a.time_phases) cudaEventRecord(g->ev_sweep0, g->stream);
+    record_sweep_event(a.ev0, g->stream, a.ev_node);
     for (int j = 0; j < 3; j++) {
         int d = a.order[j];
         PassArgs P;
@@ -209,7 +209,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
             k_pass<false><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P); note_launch();
         }
     }
-    if (a.time_phases) cudaEventRecord(g->ev_sweep1, g->stream);
+    record_sweep_event(a.ev1, g->stream, a.ev_node);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(g, e, "3-pass sweep launch");
     return VL_OK;

@@ -54,7 +54,8 @@ class vl_step_stats(ctypes.Structure):
                 ("prune_ms", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("graph_replays", ctypes.c_int64), ("capacity_regrows", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("form_used", ctypes.c_int),
-                ("tile_rows_used", ctypes.c_int), ("tune_ms", ctypes.c_double * 3)]
+                ("tile_rows_used", ctypes.c_int), ("tune_ms", ctypes.c_double * 3),
+                ("updates", ctypes.c_int64)]
 
 
 class VlError(RuntimeError):
