@@ -34,7 +34,8 @@ from paper_2504_21450_gb300 import inputs  # noqa: E402
 
 METRIC = "phase-space cell updates/s (xyz)"
 UNIT = "updates/s"
-BYTES_PER_UPDATE = {"fused": 8.0, "3pass": 8.0}  # per launch: read f once, write once
+BYTES_PER_UPDATE = {"fused": 8.0, "3pass": 8.0}  # per launch, FP32 storage: read f once, write once
+STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}  # bytes per stored value
 KERNEL = {"fused": "k_fused", "3pass": "k_pass"}
 LAUNCHES_PER_STEP = {"fused": 1, "3pass": 3}
 
@@ -243,19 +244,23 @@ def run_ours(args, cfg):
         dist.init_process_group("nccl")
     form = {"fused": vlasov.VL_FORM_FUSED, "3pass": vlasov.VL_FORM_3PASS,
             "auto": vlasov.VL_FORM_AUTO}[args.form]
+    storage = {"f32": vlasov.VL_STORE_F32, "bf16": vlasov.VL_STORE_BF16_SCALED,
+               "f16": vlasov.VL_STORE_F16_SCALED}[args.storage]
 
     host = None
     e2e_note = None
     big = state_bytes(cfg) > 40e9
     if big:
         off, ids, vals, thr = generate_host(cfg, f"cuda:{local}")
-        g = vlasov.Grid(cfg.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, device=local)
+        g = vlasov.Grid(cfg.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, storage=storage,
+                        device=local)
         g.set_blocks(off, ids, vals)
         del off, ids, vals
         e2e_note = "not measured: the state is staged in pageable host memory for this workload"
     else:
         off, ids, vals, thr = inputs.generate_torch(cfg, f"cuda:{local}")
-        g = vlasov.Grid(cfg.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, device=local)
+        g = vlasov.Grid(cfg.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, storage=storage,
+                        device=local)
         g.set_blocks(off, ids, vals)
         if args.e2e:
             host = (off.cpu().pin_memory(), ids.to(torch.int16).cpu().pin_memory(), vals.cpu().pin_memory())
@@ -344,13 +349,14 @@ def run_ours(args, cfg):
     launches_sweep = LAUNCHES_PER_STEP[form_used] * args.steps
     per_launch_updates = updates / args.steps  # every sweep launch touches every update once
     avg_launch_s = (sweep_ms / launches_sweep) / 1e3 if sweep_ms > 0 else float("nan")
-    achieved = BYTES_PER_UPDATE[form_used] * per_launch_updates / avg_launch_s / 1e9
-    workload = f"{cfg.name}"
+    bytes_per_update = BYTES_PER_UPDATE[form_used] * STORAGE_BYTES[args.storage] / 4
+    achieved = bytes_per_update * per_launch_updates / avg_launch_s / 1e9
+    workload = cfg.name if args.storage == "f32" else f"{cfg.name}-{args.storage}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "kernel": KERNEL[form_used],
                 "traffic": traffic_for(KERNEL[form_used], workload),
-                "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[form_used] * per_launch_updates,
+                "algorithmic_bytes_per_launch": bytes_per_update * per_launch_updates,
                 "avg_launch_ms": avg_launch_s * 1e3}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -359,9 +365,9 @@ def run_ours(args, cfg):
         "config": {"workload": f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} periodic cells x "
                                f"{cfg.nv[0]}x{cfg.nv[1]}x{cfg.nv[2]} velocity cells (4^3 blocks), "
                                f"dt={cfg.dt}, rel. threshold {cfg.rel_threshold:g}",
-                   "form": form_used, "order": args.order, "parallelism": f"replicas{world}",
+                   "form": form_used, "storage": args.storage, "order": args.order, "parallelism": f"replicas{world}",
                    "graph": bool(args.graph), "capacity_regrows": regrows,
-                   "l2": f"state ({updates / args.steps * 4 / 1e9:.1f} GB per copy) larger than L2; no flush",
+                   "l2": f"state ({updates / args.steps * STORAGE_BYTES[args.storage] / 1e9:.1f} GB per copy) larger than L2; no flush",
                    "blocks_per_step": updates / args.steps / 64},
         "roofline": roofline,
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
@@ -389,6 +395,8 @@ def main():
                     help="run the timed steps as one captured CUDA graph (no host sync per step)")
     ap.add_argument("--config", default="uniform", choices=sorted(inputs.CONFIGS))
     ap.add_argument("--order", default="xyz")
+    ap.add_argument("--storage", default="f32", choices=sorted(STORAGE_BYTES),
+                    help="storage of f (arithmetic is FP32 in every case)")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="override the spatial extent (smaller cases for profiling)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

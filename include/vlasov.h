@@ -54,10 +54,18 @@ typedef enum {
     VL_ESTATE = 7      /* call not valid in the grid's current state */
 } vl_status;
 
+/* Storage of f in device memory (the paper fixes none; the arithmetic of a sweep is
+ * float32 in every form).  The 16-bit forms keep q = f / s rounded to nearest even,
+ * with one power-of-two float32 scale s per block id: s is the smallest power of two
+ * >= the largest |f| of that block id in the state the step starts from (the limited
+ * scheme creates no new maximum, so codes stay near or below 1).  Every value read
+ * through this interface is float32 (q * s); every value written is rounded to the
+ * storage type.  The fused form rounds once per step, the 3-pass form after each of
+ * its three sweeps. */
 typedef enum {
     VL_STORE_F32 = 0,          /* f stored as float32 */
-    VL_STORE_BF16_SCALED = 1,  /* bfloat16 per value x float32 scale per block */
-    VL_STORE_F16_SCALED = 2    /* float16 per value x float32 scale per block */
+    VL_STORE_BF16_SCALED = 1,  /* bfloat16 code x power-of-two float32 scale per block id */
+    VL_STORE_F16_SCALED = 2    /* float16 code x power-of-two float32 scale per block id */
 } vl_storage;
 
 typedef enum {
@@ -147,7 +155,8 @@ void vl_translate_opts_default(vl_translate_opts* opts);
 
 /* Create an empty grid (no blocks).  sparsity_threshold is absolute: after each step
  * a block is kept iff its largest value is >= the threshold (Section 2); 0 keeps every
- * block that the union created.  Only VL_STORE_F32 is accepted so far.
+ * block that the union created.  storage selects float32 or a scaled 16-bit form (see
+ * vl_storage); with a 16-bit form the threshold is compared with the stored values.
  * Errors: VL_EINVAL (bad descriptor, block != {4,4,4}, storage), VL_ECUDA, VL_ENOMEM. */
 vl_status vl_grid_create(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
                          double sparsity_threshold, vl_storage storage,
@@ -158,7 +167,9 @@ vl_status vl_grid_destroy(vl_grid* grid);
 
 /* Replace the grid's state by the given per-cell lists.  on_device = 0: host pointers
  * (copied synchronously); 1: device pointers on the grid's device (read on its stream
- * before the call returns).  nblocks = cell_offsets[ncells].
+ * before the call returns).  nblocks = cell_offsets[ncells].  values are float32; with
+ * 16-bit storage they are rounded to it after the scale of each block id is taken from
+ * their largest magnitude (host values then cross to the device twice).
  * Errors: VL_EINVAL (offsets not non-decreasing, ids out of range or not strictly
  * increasing within a cell), VL_ENOMEM, VL_ECUDA. */
 vl_status vl_set_blocks(vl_grid* grid, int64_t nblocks, const int64_t* cell_offsets,
@@ -192,13 +203,15 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                        const vl_translate_opts* opts);
 
 /* Checkpoint (the paper restarts its runs from a saved state, Section 4.2): the grid's
- * state as one self-describing host buffer -- a header (magic "VLGT", format version,
- * spatial extents, velocity mesh, cell and velocity sizes, threshold, block count)
- * followed by the per-cell lists (cell_offsets, block_ids, values) of vl_get_blocks.
+ * state as one self-describing host buffer -- a header (magic "VLGT", format version 2,
+ * spatial extents, velocity mesh, cell and velocity sizes, threshold, block count,
+ * storage type, block ids) followed by the per-cell lists (cell_offsets, values,
+ * block_ids) of vl_get_blocks and the per-block-id scales and maxima of 16-bit storage,
+ * so that a restarted run continues bit for bit.
  * vl_export with buf == NULL stores the required size in *size; otherwise *size must
  * hold the buffer's size (VL_ECAPACITY when too small) and receives the bytes written.
- * vl_import replaces the state of a grid with the same extents and velocity mesh
- * (VL_EINVAL otherwise, or for a damaged buffer). */
+ * vl_import replaces the state of a grid with the same extents, velocity mesh and
+ * storage type (VL_EINVAL otherwise, or for a damaged buffer). */
 vl_status vl_export(vl_grid* grid, void* buf, size_t* size);
 vl_status vl_import(vl_grid* grid, const void* buf, size_t size);
 

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "grid.h"
 
@@ -120,6 +121,7 @@ vl_status enqueue_step(Grid* g, StepArgs a, bool fused, bool graph, int64_t capa
     a.ctr = ctr;
     cudaMemsetAsync(ctr, 0, sizeof(StepCounters), g->stream);
     launch_union(g, A, B);
+    launch_out_scale(g, A, B);
     if (graph) {
         launch_index(g, B);
         launch_capacity_check(g, B, capacity, ctr);
@@ -204,7 +206,6 @@ uint64_t mix(uint64_t h, uint64_t v)
 // the pools grow and the remaining steps run again.
 vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t capacity, vl_step_stats* S)
 {
-    const GridGeom& G = g->geom;
     int64_t cap = capacity > 0 ? capacity
                                : std::max<int64_t>(g->lay[g->cur].total + g->lay[g->cur].total / 4, 1024);
     if (!g->abort_flag) {
@@ -352,6 +353,7 @@ uint64_t tune_key(const Grid* g, const StepArgs& a)
         k = mix(k, (uint64_t)a.order[d]);
     }
     k = mix(k, (uint64_t)a.limiter);
+    k = mix(k, (uint64_t)g->codec);
     // sparsity class: slots per cell rounded to a power of two
     const int64_t t = std::max<int64_t>(g->lay[g->cur].total, 1);
     int lg = 0;
@@ -455,8 +457,8 @@ vl_status vl_grid_create(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
         g_create_error = "vl_grid_create: more than 2^31 spatial cells";
         return VL_EINVAL;
     }
-    if (storage != VL_STORE_F32) {
-        g_create_error = "vl_grid_create: only VL_STORE_F32 is implemented";
+    if (storage != VL_STORE_F32 && storage != VL_STORE_BF16_SCALED && storage != VL_STORE_F16_SCALED) {
+        g_create_error = "vl_grid_create: unknown storage type";
         return VL_EINVAL;
     }
     if (!(sparsity_threshold >= 0.0) || !std::isfinite(sparsity_threshold)) {
@@ -472,6 +474,8 @@ vl_status vl_grid_create(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
     g->vmesh = *vmesh;
     g->threshold = sparsity_threshold;
     g->storage = storage;
+    g->codec = storage == VL_STORE_BF16_SCALED ? 1 : storage == VL_STORE_F16_SCALED ? 2 : 0;
+    g->esize = g->codec ? 2 : 4;
     if (device) g->dev = *device;
     else std::memset(&g->dev, 0, sizeof(g->dev));
     g->stream = (cudaStream_t)g->dev.stream;
@@ -607,6 +611,8 @@ struct CheckpointHeader {
     double vmin[3], dv[3], dx[3];
     double threshold;
     int64_t nblocks;
+    int32_t storage;  // version 2: vl_storage of the values' scales below
+    int32_t nb;       // version 2: block ids (length of the scale and vmax arrays)
 };
 }  // namespace
 
@@ -619,7 +625,9 @@ vl_status vl_export(vl_grid* grid, void* buf, size_t* size)
     vl_status st = get_block_count(g, &M);
     if (st != VL_OK) return st;
     const int64_t N = g->geom.N;
-    const size_t need = sizeof(CheckpointHeader) + (size_t)(N + 1) * 8 + (size_t)M * 2 + (size_t)M * 256 + 8;
+    const int nb = g->geom.nb;
+    const size_t need = sizeof(CheckpointHeader) + (size_t)(N + 1) * 8 + (size_t)M * 2 + (size_t)M * 256 +
+                        (size_t)nb * 8 + 8;
     if (!buf) {
         *size = need;
         return VL_OK;
@@ -628,7 +636,9 @@ vl_status vl_export(vl_grid* grid, void* buf, size_t* size)
                                                      " bytes, " + std::to_string(need) + " needed");
     CheckpointHeader h;
     std::memcpy(h.magic, "VLGT", 4);
-    h.version = 1;
+    h.version = 2;
+    h.storage = (int32_t)g->storage;
+    h.nb = nb;
     for (int d = 0; d < 3; d++) {
         h.n[d] = g->space.n[d];
         h.nv[d] = g->vmesh.nv[d];
@@ -646,8 +656,16 @@ vl_status vl_export(vl_grid* grid, void* buf, size_t* size)
     float* vals = reinterpret_cast<float*>(p);
     p += (size_t)M * 256;
     uint16_t* ids = reinterpret_cast<uint16_t*>(p);
+    p += (size_t)M * 2;
     st = get_blocks(g, M, off, ids, vals, 0);
     if (st != VL_OK) return st;
+    // scales of the 16-bit codes and the per-block-id maxima that set the next step's
+    // scales: restoring both makes a restarted run continue bit for bit
+    const Layout& L = g->lay[g->cur];
+    cudaMemcpyAsync(p, L.scale, (size_t)nb * 4, cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(p + (size_t)nb * 4, L.vmax, (size_t)nb * 4, cudaMemcpyDeviceToHost, g->stream);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_export");
     *size = need;
     return VL_OK;
 }
@@ -660,14 +678,16 @@ vl_status vl_import(vl_grid* grid, const void* buf, size_t size)
     CheckpointHeader h;
     if (size < sizeof(h)) return fail(g, VL_EINVAL, "vl_import: buffer too small");
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "VLGT", 4) != 0 || h.version != 1)
+    if (std::memcmp(h.magic, "VLGT", 4) != 0 || h.version != 2)
         return fail(g, VL_EINVAL, "vl_import: not a checkpoint of this library");
+    if (h.storage != (int32_t)g->storage || h.nb != g->geom.nb)
+        return fail(g, VL_EINVAL, "vl_import: storage type of the checkpoint differs from the grid's");
     for (int d = 0; d < 3; d++)
         if (h.n[d] != g->space.n[d] || h.nv[d] != g->vmesh.nv[d] || h.vmin[d] != g->vmesh.vmin[d] ||
             h.dv[d] != g->vmesh.dv[d])
             return fail(g, VL_EINVAL, "vl_import: grid extents or velocity mesh differ");
     const int64_t N = g->geom.N, M = h.nblocks;
-    if (M < 0 || size < sizeof(h) + (size_t)(N + 1) * 8 + (size_t)M * 258)
+    if (M < 0 || size < sizeof(h) + (size_t)(N + 1) * 8 + (size_t)M * 258 + (size_t)h.nb * 8)
         return fail(g, VL_EINVAL, "vl_import: truncated checkpoint");
     const char* p = static_cast<const char*>(buf) + sizeof(h);
     const int64_t* off = reinterpret_cast<const int64_t*>(p);
@@ -675,7 +695,12 @@ vl_status vl_import(vl_grid* grid, const void* buf, size_t size)
     const float* vals = reinterpret_cast<const float*>(p);
     p += (size_t)M * 256;
     const uint16_t* ids = reinterpret_cast<const uint16_t*>(p);
-    vl_status st = set_blocks(g, M, off, ids, vals, 0);
+    p += (size_t)M * 2;
+    std::vector<float> scale((size_t)h.nb);
+    std::vector<unsigned> vmax((size_t)h.nb);
+    std::memcpy(scale.data(), p, (size_t)h.nb * 4);
+    std::memcpy(vmax.data(), p + (size_t)h.nb * 4, (size_t)h.nb * 4);
+    vl_status st = set_blocks(g, M, off, ids, vals, 0, scale.data(), vmax.data());
     if (st == VL_OK) {
         g->stats.mass = NAN;
         g->present = M;
@@ -790,6 +815,9 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
             bool complete = true;
             for (int c = 0; c < 3 && st == VL_OK; c++) {
                 if (cand_ty[c] == 16 && a.order[2] != 2) continue;  // 16-row tiles need a z-last order
+                // 16-bit storage: the 3-pass form rounds to storage after every sweep, so
+                // it is not the same computation as the fused form; only tile sizes are tuned
+                if (cand_form[c] == VL_FORM_3PASS && g->codec != 0) continue;
                 if (nsteps - done < 2) {
                     complete = false;
                     break;

@@ -16,7 +16,11 @@
 //     chunks per q, which keeps the 16-byte vector loads of a tile row coalesced.
 //   * dense[b]: bit 0 = every cell has a slot for b (rank = cell index), bit 1 = every
 //     cell holds b (kbits all set); sweeps skip the bitmaps when both are set.
+//   * Values are float32, or bfloat16 / float16 codes q of f = q * scale[b] with one
+//     power-of-two scale per block id (see Codec).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,8 +36,56 @@ struct LayoutView {
     const uint32_t* cnt;
     const int64_t* base;
     const uint8_t* dense;
-    float* pool;
+    void* pool;       // values in the grid's storage type (Codec<k>::T)
+    float* scale;     // [nb] power-of-two scale of the codes of block id b (16-bit storage)
+    unsigned* vmax;   // [nb] max |f| of block id b written so far (float bits), or nullptr
 };
+
+// Storage codecs.  FP32 storage keeps f.  The 16-bit forms keep q = f / s rounded to
+// nearest even in bfloat16 or float16, with s a power of two per block id: dividing
+// and multiplying by s is exact in FP32, so the rounding to 16 bits is the only error,
+// and the arithmetic of a sweep stays FP32.  s is at least the largest |f| of the block
+// id (see pow2_at_least), which keeps float16 codes of small values in its normal
+// range; codes a little above 1 (rounding, overshoot without the limiter) are still
+// representable in both formats.
+template <int kCodec>
+struct Codec;
+template <>
+struct Codec<0> {
+    using T = float;
+    static __device__ __forceinline__ float dec(T q, float) { return q; }
+    static __device__ __forceinline__ T enc(float f, float) { return f; }
+};
+template <>
+struct Codec<1> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float dec(T q, float s) { return __bfloat162float(q) * s; }
+    static __device__ __forceinline__ T enc(float f, float inv) { return __float2bfloat16_rn(f * inv); }
+};
+template <>
+struct Codec<2> {
+    using T = __half;
+    static __device__ __forceinline__ float dec(T q, float s) { return __half2float(q) * s; }
+    static __device__ __forceinline__ T enc(float f, float inv) { return __float2half_rn(f * inv); }
+};
+
+// Smallest power of two >= m (m >= 0), from the FP32 bit fields; 1 for m = 0, at least
+// the smallest normal number, at most 2^127.
+__host__ __device__ inline float pow2_at_least(float m)
+{
+    if (!(m > 0.0f)) return 1.0f;
+    union {
+        float f;
+        unsigned u;
+    } b;
+    b.f = m;
+    unsigned e = b.u >> 23;
+    if (e == 0) e = 1;                           // subnormal: 2^-126 covers it
+    else if ((b.u & 0x7fffffu) != 0) e += 1;     // not a power of two: next one up
+    if (e > 254) e = 254;
+    b.u = e << 23;
+    return b.f;
+}
 
 struct GridGeom {
     const int* abort;  // sticky device flag of a captured step sequence (nullptr: none);

@@ -39,12 +39,13 @@ constexpr int TX = 16;
 constexpr int NT = 512;
 constexpr int NST = 3;               // pipeline stages of staged planes
 constexpr int EX = TX + 2 * H;       // 22 halo columns
-constexpr int SROW = EX * NV + 16;   // padded stage row (floats), 16 mod 32
+constexpr int SROW = EX * NV + 16;   // padded stage row (values), 16 mod 32
 constexpr int XROW = TX * NV + 16;   // padded sweep-0 output row
 
-template <int TY_>
+template <int TY_, int ES_ = 4>
 struct Shape {
     static constexpr int TY = TY_;
+    static constexpr int ES = ES_;            // bytes per staged value (storage type)
     static constexpr int EY = TY + 2 * H;
     static constexpr int NX = EY * NV;        // threads of sweep 0
     static constexpr int NLD = NT - NX;       // threads staging planes meanwhile
@@ -53,7 +54,7 @@ struct Shape {
     static constexpr int STAGE = EY * SROW;
     static constexpr int XBUF = EY * XROW;
     static constexpr int TABS = 2 * EX + 2 * EY;
-    static constexpr int SMEM = (NST * STAGE + XBUF) * 4 + TABS * 4 + 2 * TX * TY * 4 + 2 * 16 * 4 + 64;
+    static constexpr int SMEM = NST * STAGE * ES + XBUF * 4 + TABS * 4 + 2 * TX * TY * 4 + 2 * 16 * 4 + 64;
     static_assert(NX < NT, "sweep-0 rows must leave threads to stage planes");
     static_assert(NH * TX * NV == NT && NH * L == TY, "sweep-1 segments must tile the CTA");
 };
@@ -146,15 +147,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // real copy time (a plane is a few tens of kB), so reaching it means a fault upstream.
 constexpr unsigned kMaxPolls = 1u << 24;
 
-template <int TY, bool kLim, bool kZUni>
+template <int TY, bool kLim, bool kZUni, int kCodec>
 __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 {
-    using S = Shape<TY>;
+    using C = Codec<kCodec>;
+    using T = typename C::T;
+    using S = Shape<TY, (int)sizeof(T)>;
+    constexpr int PC = NV * (int)sizeof(T) / 16;  // 16-byte pieces per staged cell
     constexpr int EY = S::EY;
     constexpr int NLD = S::NLD, L = S::L;
     extern __shared__ __align__(16) float smem[];
-    float* stage = smem;
-    float* xbuf = stage + NST * S::STAGE;
+    T* stage = reinterpret_cast<T*>(smem);
+    float* xbuf = reinterpret_cast<float*>(stage + NST * S::STAGE);
     int* px0 = reinterpret_cast<int*>(xbuf + S::XBUF);
     int* pr0 = px0 + EX;
     int* px1 = pr0 + EX;
@@ -222,6 +226,12 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         const int64_t ibase = ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * NV;
         const int64_t obase = ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * NV;
         const int64_t okeep = (int64_t)P.out.base[b];
+        const T* ipool = static_cast<const T*>(P.in.pool);
+        T* opool = static_cast<T*>(P.out.pool);
+        // 16-bit storage: scales of the codes read and written (powers of two)
+        const float sc_in = kCodec ? P.in.scale[b] : 1.0f;
+        const float sc_out = kCodec ? P.out.scale[b] : 1.0f;
+        const float inv_out = 1.0f / sc_out;
 
         // contiguous runs of a halo row along axis 0 (split at the periodic wrap)
         if (tid == 0 && (bulk || sbulk)) {
@@ -276,24 +286,24 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             if (s < nsteps) {
                 const int pz = wrapi(plane_of(s), n2);
                 const int x2 = xpart(a2, pz), r2 = rpart(a2, pz, ny);
-                float* st = stage + (s % NST) * S::STAGE;
+                T* st = stage + (s % NST) * S::STAGE;
                 if (bulk) {
                     // one lane expects the plane's bytes, then lane u1 copies halo row u1
                     // as one bulk copy per contiguous run
                     uint64_t* bar = &s_bar[(gstep + s) % NST];
                     if (ltid == 0) {
                         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                        mbar_expect_tx(bar, (unsigned)(EX * EY * NV * 4));
+                        mbar_expect_tx(bar, (unsigned)(EX * EY * NV * sizeof(T)));
                     }
                     __syncwarp();
                     if (ltid < EY) {
                         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                         const int64_t row = (int64_t)pr1[ltid] + r2;
-                        const float* src = P.in.pool + ibase + row * G.n[0] * NV;
-                        float* dst = st + ltid * SROW;
+                        const T* src = ipool + ibase + row * G.n[0] * NV;
+                        T* dst = st + ltid * SROW;
                         for (int k = 0; k < s_nrun; k++)
                             bulk_g2s(dst + s_run[k][0] * NV, src + s_run[k][1] * NV,
-                                     (unsigned)(s_run[k][2] * NV * 4), bar);
+                                     (unsigned)(s_run[k][2] * NV * sizeof(T)), bar);
                     }
                 } else if (sbulk) {
                     // lane u1 stages halo row u1: one bulk copy per run of present cells
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                         const uint64_t* krow = P.in.kbits + (int64_t)b * G.RW + row * G.W;
                         const uint64_t* urow = P.in.ubits + (int64_t)b * G.RW + row * G.W;
                         const uint32_t* wrow = P.in.woff + (int64_t)b * G.RW + row * G.W;
-                        float* dst = st + ltid * SROW;
+                        T* dst = st + ltid * SROW;
                         unsigned bytes = 0;
                         for (int pass = 0; pass < 2; pass++) {
                             for (int k = 0; k < s_nrun; k++) {
@@ -318,22 +328,20 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                                         if (pass == 1) {
                                             float4* z = reinterpret_cast<float4*>(dst + (u0 + u) * NV);
                                             const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-                                            z[0] = zero;
-                                            z[1] = zero;
-                                            z[2] = zero;
-                                            z[3] = zero;
+#pragma unroll
+                                            for (int k2 = 0; k2 < PC; k2++) z[k2] = zero;
                                         }
                                         u++;
                                         continue;
                                     }
                                     const int rl = run_of_ones(krow, urow, x, len - u);
                                     if (pass == 0) {
-                                        bytes += (unsigned)(rl * NV * 4);
+                                        bytes += (unsigned)(rl * NV * sizeof(T));
                                     } else {
                                         const int64_t r = (int64_t)wrow[x >> 6] +
                                                           __popcll(urow[x >> 6] & ((1ull << (x & 63)) - 1ull));
-                                        bulk_g2s(dst + (u0 + u) * NV, P.in.pool + ibase + r * NV,
-                                                 (unsigned)(rl * NV * 4), bar);
+                                        bulk_g2s(dst + (u0 + u) * NV, ipool + ibase + r * NV,
+                                                 (unsigned)(rl * NV * sizeof(T)), bar);
                                     }
                                     u += rl;
                                 }
@@ -344,14 +352,15 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     __syncwarp();
                     if (ltid == 0) mbar_arrive(bar);
                 } else {
-                    for (int k = ltid; k < EX * EY * 4; k += NLD) {
-                        int cell = k >> 2, piece = k & 3;
+                    for (int k = ltid; k < EX * EY * PC; k += NLD) {
+                        int cell = k / PC, piece = k - cell * PC;
                         int u1 = cell / EX, u0 = cell - u1 * EX;
                         int x = px0[u0] + px1[u1] + x2;
                         int64_t row = (int64_t)pr0[u0] + pr1[u1] + r2;
                         int64_t r = dense_in ? row * G.n[0] + x : cell_rank(P.in, G, b, x, row, true);
-                        const float* src = r >= 0 ? P.in.pool + ibase + r * NV + 4 * piece : P.in.pool;
-                        cp_async16(st + u1 * SROW + u0 * NV + 4 * piece, src, r >= 0 ? 16 : 0);
+                        constexpr int PE = 16 / (int)sizeof(T);  // values per piece
+                        const T* src = r >= 0 ? ipool + ibase + r * NV + PE * piece : ipool;
+                        cp_async16(st + u1 * SROW + u0 * NV + PE * piece, src, r >= 0 ? 16 : 0);
                     }
                 }
             }
@@ -415,6 +424,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 #pragma unroll
         for (int j = 0; j < (kZUni ? 1 : L); j++) zg[j].reset();
         float msum = 0.0f, mcomp = 0.0f;  // Kahan-compensated FP32 mass of this thread
+        float vmx = 0.0f;                 // largest |stored value| (16-bit storage)
 
         if (loader) {
             issue_plane(0);
@@ -428,20 +438,20 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             __syncthreads();  // plane s staged; previous readers of xbuf done
             if (!loader) {
                 // sweep 0 along axis 0 on halo row `hi`
-                const float* line = stage + (s % NST) * S::STAGE + hi * SROW + v;
+                const T* line = stage + (s % NST) * S::STAGE + hi * SROW + v;
                 float* xo = xbuf + hi * XROW + v;
                 Walk<kLim> wk;
                 wk.reset();
                 if (kw[0].up) {
 #pragma unroll
                     for (int t = 0; t < TX + 5; t++) {
-                        float r = wk.push(line[t * NV], kw[0]);
+                        float r = wk.push(C::dec(line[t * NV], sc_in), kw[0]);
                         if (t >= 5) xo[(t - 5) * NV] = r;
                     }
                 } else {
 #pragma unroll
                     for (int t = 0; t < TX + 5; t++) {
-                        float r = wk.push(line[(TX + 5 - t) * NV], kw[0]);
+                        float r = wk.push(C::dec(line[(TX + 5 - t) * NV], sc_in), kw[0]);
                         if (t >= 5) xo[(TX + 4 - t) * NV] = r;
                     }
                 }
@@ -454,7 +464,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             // sweep 1 along axis 1 over rows j0..j0+L-1 of tile column ci, each output
             // pushed straight into the streamed window of its cell (sweep 2)
             const int zo = out_of(s);
-            float* dst = P.out.pool + obase + v +
+            T* dst = opool + obase + v +
                          ((int64_t)(t0 + ci) * P.stride[a0] + (int64_t)(t1 + j0) * P.stride[a1] +
                           (int64_t)zo * P.stride[a2]) * NV;
             const int64_t dstep = P.stride[a1] * NV;
@@ -467,8 +477,13 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 if (kZUni) res = zu[kZUni ? jj : 0].push(yv, kw[2]);
                 else res = zg[kZUni ? 0 : jj].push(yv, ks2);
                 if (kEmit) {
+                    const T code = C::enc(res, inv_out);
+                    if (kCodec) {
+                        res = C::dec(code, sc_out);  // the value the state now holds
+                        vmx = fmaxf(vmx, fabsf(res));
+                    }
                     if (fast) {
-                        dst[jj * dstep] = res;
+                        dst[jj * dstep] = code;
                         psum += res;
                     } else {
                         int64_t r = -1;
@@ -478,8 +493,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                             r = orow[jj * TX];
                         }
                         if (r >= 0) {
-                            if (dense_out) dst[jj * dstep] = res;
-                            else P.out.pool[obase + r * NV + v] = res;
+                            if (dense_out) dst[jj * dstep] = code;
+                            else opool[obase + r * NV + v] = code;
                             psum += res;
                         }
                     }
@@ -522,6 +537,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         double m = (double)msum;
         for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
         if (lane == 0 && m != 0.0) atomicAdd(&P.ctr->mass, m);
+        if (kCodec) {
+            unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
+            if (lane == 0 && u) atomicMax(&P.out.vmax[b], u);
+        }
     }
 }
 
@@ -585,11 +604,11 @@ __global__ void k_tile_items(int64_t ntiles, int nb, const uint32_t* __restrict_
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-template <int TY, bool kLim, bool kZUni>
+template <int TY, bool kLim, bool kZUni, int kCodec = 0>
 vl_status launch_fused(Grid* g, const FusedArgs& P)
 {
-    auto kern = k_fused<TY, kLim, kZUni>;
-    const int smem = Shape<TY>::SMEM;
+    auto kern = k_fused<TY, kLim, kZUni, kCodec>;
+    const int smem = Shape<TY, (int)sizeof(typename Codec<kCodec>::T)>::SMEM;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int nsm = 0, per_sm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
@@ -679,13 +698,16 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.keepq = B.keepq;
     P.ctr = a.ctr;
     record_sweep_event(a.ev0, g->stream, a.ev_node);
-    vl_status st;
-    if (zuni && ty == 16)
-        st = a.limiter ? launch_fused<16, true, true>(g, P) : launch_fused<16, false, true>(g, P);
-    else if (zuni)
-        st = a.limiter ? launch_fused<8, true, true>(g, P) : launch_fused<8, false, true>(g, P);
-    else
-        st = a.limiter ? launch_fused<8, true, false>(g, P) : launch_fused<8, false, false>(g, P);
+    vl_status st = VL_OK;
+    with_codec(g->codec, [&](auto c) {
+        constexpr int kc = decltype(c)::value;
+        if (zuni && ty == 16)
+            st = a.limiter ? launch_fused<16, true, true, kc>(g, P) : launch_fused<16, false, true, kc>(g, P);
+        else if (zuni)
+            st = a.limiter ? launch_fused<8, true, true, kc>(g, P) : launch_fused<8, false, true, kc>(g, P);
+        else
+            st = a.limiter ? launch_fused<8, true, false, kc>(g, P) : launch_fused<8, false, false, kc>(g, P);
+    });
     record_sweep_event(a.ev1, g->stream, a.ev_node);
     return st;
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
 #include <vector>
 #include <stdint.h>
 
@@ -24,12 +25,14 @@ struct Layout {
     int64_t* base = nullptr;     // [nb + 1]
     uint8_t* dense = nullptr;    // [nb]
     uint32_t* kcnt = nullptr;    // [nb] kept blocks per id
-    float* pool = nullptr;       // [capacity * 64]
+    void* pool = nullptr;        // [capacity * 64] values in the storage type
+    float* scale = nullptr;      // [nb] power-of-two scale of the 16-bit codes
+    unsigned* vmax = nullptr;    // [nb] max |f| per block id (float bits)
     uint8_t* keepq = nullptr;    // [capacity * 4] per-chunk keep flags of the last sweep
     int64_t capacity = 0;        // blocks the pool can hold
     int64_t total = 0;           // slots in use (host copy)
 
-    LayoutView view() const { return LayoutView{ubits, kbits, woff, cnt, base, dense, pool}; }
+    LayoutView view() const { return LayoutView{ubits, kbits, woff, cnt, base, dense, pool, scale, vmax}; }
 };
 
 struct Grid {
@@ -37,6 +40,8 @@ struct Grid {
     vl_vmesh_desc vmesh;
     double threshold = 0.0;
     vl_storage storage = VL_STORE_F32;
+    int codec = 0;      // Codec<codec>: 0 float32, 1 bfloat16, 2 float16
+    size_t esize = 4;   // bytes per stored value
     vl_device dev;
     cudaStream_t stream = nullptr;
     GridGeom geom;
@@ -91,6 +96,9 @@ vl_status cuda_fail(Grid* g, cudaError_t e, const char* what);
 vl_status layout_alloc_meta(Grid* g, Layout& L);
 void layout_free(Grid* g, Layout& L);
 vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks);
+// 16-bit storage: scale of the next layout's codes from the current layout's largest
+// values (translation with the limiter creates no new maximum), and its vmax cleared.
+void launch_out_scale(Grid* g, const Layout& cur, Layout& next);
 // Like layout_ensure_pool, but keeps the L.total blocks the pool holds.
 vl_status layout_grow_pool(Grid* g, Layout& L, int64_t blocks);
 // Counts, offsets and dense flags of L from its ubits (woff, cnt, base, dense);
@@ -105,8 +113,11 @@ void launch_index(Grid* g, Layout& L);
 void launch_pack_keep(Grid* g, Layout& next, StepCounters* ctr);
 // Sets the abort flag and ctr->error bit 3 when L's slot total exceeds capacity.
 void launch_capacity_check(Grid* g, const Layout& L, int64_t capacity, StepCounters* ctr);
+// scale_host / vmax_host (host, nb each, optional): codes of 16-bit storage use these
+// scales instead of ones derived from the values, and the maxima are restored (import).
 vl_status set_blocks(Grid* g, int64_t nblocks, const int64_t* off, const uint16_t* ids,
-                     const float* vals, int on_device);
+                     const float* vals, int on_device, const float* scale_host = nullptr,
+                     const unsigned* vmax_host = nullptr);
 vl_status get_block_count(Grid* g, int64_t* n);
 vl_status get_blocks(Grid* g, int64_t capacity, int64_t* off, uint16_t* ids, float* vals,
                      int on_device);
@@ -134,6 +145,16 @@ struct StepArgs {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the sweep kernels when set
     bool ev_node = false;  // inside a stream capture: record as event record nodes
 };
+// Calls f(std::integral_constant<int, k>{}) for storage codec k (0 float32, 1 bfloat16,
+// 2 float16), so that one launch site instantiates the kernel for every codec.
+template <class F>
+inline void with_codec(int codec, F&& f)
+{
+    if (codec == 1) f(std::integral_constant<int, 1>{});
+    else if (codec == 2) f(std::integral_constant<int, 2>{});
+    else f(std::integral_constant<int, 0>{});
+}
+
 // Records ev on s; inside a capture as an event record node, which the graph records on
 // every replay (a plain record there would only mark a capture dependency).
 inline void record_sweep_event(cudaEvent_t ev, cudaStream_t s, bool node)

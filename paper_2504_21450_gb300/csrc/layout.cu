@@ -186,6 +186,7 @@ constexpr int kPackThreads = 256;
 // Sparsity rule: a slot of the new layout stays iff any of its four chunks had a value
 // >= threshold (the per-chunk flags are written by the sweep epilogue).  Removed blocks
 // add their FP64 mass (sum of the 64 averages) to the dropped mass.
+template <int kCodec>
 __global__ void k_pack_keep(GridGeom G, LayoutView L, const uint8_t* __restrict__ keepq,
                             uint64_t* __restrict__ kout, uint32_t* __restrict__ kcnt,
                             StepCounters* __restrict__ ctr, int64_t chunks_per_seg)
@@ -216,14 +217,12 @@ __global__ void k_pack_keep(GridGeom G, LayoutView L, const uint8_t* __restrict_
                 kept++;
             } else {
                 drop++;
+                using T = typename Codec<kCodec>::T;
+                const float sc = kCodec ? L.scale[b] : 1.0f;
                 double s = 0.0;
                 for (int q = 0; q < 4; q++) {
-                    const float4* p = reinterpret_cast<const float4*>(
-                        L.pool + ((bb * 4 + (int64_t)q * cb + rank) * kChunk));
-                    for (int j = 0; j < 4; j++) {
-                        float4 v = p[j];
-                        s += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
-                    }
+                    const T* p = static_cast<const T*>(L.pool) + (bb * 4 + (int64_t)q * cb + rank) * kChunk;
+                    for (int j = 0; j < kChunk; j++) s += (double)Codec<kCodec>::dec(p[j], sc);
                 }
                 dmass += s;
             }
@@ -297,6 +296,7 @@ __global__ void k_mark(GridGeom G, const int64_t* __restrict__ off, const uint16
              (unsigned long long)(1ull << (x & 63)));
 }
 
+template <int kCodec>
 __global__ void k_scatter(GridGeom G, LayoutView L, const uint16_t* __restrict__ ids,
                           const int64_t* __restrict__ cell_of, const float* __restrict__ vals,
                           int64_t t0, int64_t M)
@@ -310,7 +310,8 @@ __global__ void k_scatter(GridGeom G, LayoutView L, const uint16_t* __restrict__
     int x = (int)(c % G.n[0]);
     int64_t rank = cell_rank(L, G, b, x, c / G.n[0], false);
     int64_t dst = ((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15);
-    L.pool[dst] = vals[i];
+    static_cast<typename Codec<kCodec>::T*>(L.pool)[dst] =
+        Codec<kCodec>::enc(vals[i], kCodec ? 1.0f / L.scale[b] : 1.0f);
 }
 
 // ---- layout -> per-cell lists ----------------------------------------------------
@@ -376,6 +377,7 @@ __global__ void k_fill_ids(GridGeom G, Window Wn, LayoutView L, const int64_t* _
     }
 }
 
+template <int kCodec>
 __global__ void k_gather(LayoutView L, const uint16_t* __restrict__ ids,
                          const int64_t* __restrict__ rank_of, float* __restrict__ vals, int64_t M)
 {
@@ -384,7 +386,10 @@ __global__ void k_gather(LayoutView L, const uint16_t* __restrict__ ids,
     int64_t t = i >> 6;
     int v = (int)(i & 63);
     int b = ids[t];
-    vals[i] = L.pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank_of[t]) * kChunk + (v & 15)];
+    const auto* pool = static_cast<const typename Codec<kCodec>::T*>(L.pool);
+    vals[i] = Codec<kCodec>::dec(
+        pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank_of[t]) * kChunk + (v & 15)],
+        kCodec ? L.scale[b] : 1.0f);
 }
 
 // ---- moments -----------------------------------------------------------------------
@@ -399,6 +404,7 @@ __device__ __forceinline__ double warp_sum(double x)
 }
 
 // One warp per cell; two passes over the cell's blocks (n and nV, then P about V).
+template <int kCodec>
 __global__ void k_moments(GridGeom G, LayoutView L, VMesh V, double* __restrict__ out)
 {
     int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -424,7 +430,10 @@ __global__ void k_moments(GridGeom G, LayoutView L, VMesh V, double* __restrict_
                 int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
                 for (int h = 0; h < 2; h++) {
                     int v = lane + 32 * h;
-                    float f = L.pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15)];
+                    const auto* pool = static_cast<const typename Codec<kCodec>::T*>(L.pool);
+                    float f = Codec<kCodec>::dec(
+                        pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15)],
+                        kCodec ? L.scale[b] : 1.0f);
                     double vel[3] = {V.vmin[0] + (bx * 4 + (v & 3) + 0.5) * V.dv[0],
                                      V.vmin[1] + (by * 4 + ((v >> 2) & 3) + 0.5) * V.dv[1],
                                      V.vmin[2] + (bz * 4 + (v >> 4) + 0.5) * V.dv[2]};
@@ -449,6 +458,45 @@ __global__ void k_moments(GridGeom G, LayoutView L, VMesh V, double* __restrict_
         o[0] = s0 * dv3;
         for (int d = 0; d < 3; d++) o[1 + d] = s1[d] * dv3;
         for (int d = 0; d < 3; d++) o[4 + d] = s2[d] * dv3;
+    }
+}
+
+__global__ void k_fill_f32(float* __restrict__ p, float v, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// Largest |f| per block id of input blocks t0 .. t0+m-1 (64 values each), one warp per
+// block: two values per lane, a warp maximum, one atomic per block.
+__global__ void k_block_vmax(const uint16_t* __restrict__ ids, const float* __restrict__ vals,
+                             int64_t t0, int64_t m, unsigned* __restrict__ vmax)
+{
+    int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= m) return;
+    float a = fmaxf(fabsf(vals[t * 64 + lane]), fabsf(vals[t * 64 + 32 + lane]));
+    unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(a));
+    if (lane == 0 && u) atomicMax(&vmax[ids[t0 + t]], u);
+}
+
+// scale[b] = smallest power of two >= max |f| of block id b
+__global__ void k_scale_from_vmax(const unsigned* __restrict__ vmax, float* __restrict__ scale, int nb)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) scale[b] = pow2_at_least(__uint_as_float(vmax[b]));
+}
+
+// Next layout of a step with 16-bit storage: scale from the current layout's maxima,
+// maxima of the next layout cleared (the step's last sweep accumulates them).
+__global__ void k_out_scale(const unsigned* __restrict__ vmax_cur, float* __restrict__ scale_next,
+                            unsigned* __restrict__ vmax_next, int nb, const int* abort)
+{
+    if (aborted(abort)) return;
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) {
+        scale_next[b] = pow2_at_least(__uint_as_float(vmax_cur[b]));
+        vmax_next[b] = 0u;
     }
 }
 
@@ -505,8 +553,14 @@ vl_status layout_alloc_meta(Grid* g, Layout& L)
     L.base = (int64_t*)g->alloc(((size_t)G.nb + 1) * 8);
     L.dense = (uint8_t*)g->alloc((size_t)G.nb);
     L.kcnt = (uint32_t*)g->alloc((size_t)G.nb * 4);
-    if (!L.ubits || !L.kbits || !L.woff || !L.wcount || !L.cnt || !L.base || !L.dense || !L.kcnt)
+    L.scale = (float*)g->alloc((size_t)G.nb * 4);
+    L.vmax = (unsigned*)g->alloc((size_t)G.nb * 4);
+    if (!L.ubits || !L.kbits || !L.woff || !L.wcount || !L.cnt || !L.base || !L.dense || !L.kcnt ||
+        !L.scale || !L.vmax)
         return fail(g, VL_ENOMEM, "allocation of the block bitmaps failed");
+    k_fill_f32<<<nblk(G.nb, 256), 256, 0, g->stream>>>(L.scale, 1.0f, G.nb);
+    note_launch();
+    cudaMemsetAsync(L.vmax, 0, (size_t)G.nb * 4, g->stream);
     cudaMemsetAsync(L.ubits, 0, words * 8, g->stream);
     cudaMemsetAsync(L.kbits, 0, words * 8, g->stream);
     cudaMemsetAsync(L.dense, 0, (size_t)G.nb, g->stream);
@@ -523,6 +577,8 @@ void layout_free(Grid* g, Layout& L)
     g->release(L.base);
     g->release(L.dense);
     g->release(L.kcnt);
+    g->release(L.scale);
+    g->release(L.vmax);
     g->release(L.pool);
     g->release(L.keepq);
     L = Layout{};
@@ -534,12 +590,12 @@ vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks)
     int64_t cap = blocks + blocks / 32 + 64;
     g->release(L.pool);
     g->release(L.keepq);
-    L.pool = (float*)g->alloc((size_t)cap * 64 * sizeof(float));
+    L.pool = g->alloc((size_t)cap * 64 * g->esize);
     L.keepq = (uint8_t*)g->alloc((size_t)cap * 4);
     if (!L.pool || !L.keepq) {
         L.capacity = 0;
         return fail(g, VL_ENOMEM, "allocation of the phase-space pool failed (" +
-                                      std::to_string(cap * 256) + " bytes)");
+                                      std::to_string(cap * 64 * (int64_t)g->esize) + " bytes)");
     }
     L.capacity = cap;
     return VL_OK;
@@ -556,15 +612,15 @@ void launch_index(Grid* g, Layout& L)
 vl_status layout_grow_pool(Grid* g, Layout& L, int64_t blocks)
 {
     if (blocks <= L.capacity && L.pool) return VL_OK;
-    float* pool = (float*)g->alloc((size_t)blocks * 64 * sizeof(float));
+    void* pool = g->alloc((size_t)blocks * 64 * g->esize);
     uint8_t* keepq = (uint8_t*)g->alloc((size_t)blocks * 4);
     if (!pool || !keepq) {
         g->release(pool);
         g->release(keepq);
-        return fail(g, VL_ENOMEM, "growing the phase-space pool failed (" + std::to_string(blocks * 256) + " bytes)");
+        return fail(g, VL_ENOMEM, "growing the phase-space pool failed (" + std::to_string(blocks * 64 * (int64_t)g->esize) + " bytes)");
     }
     if (L.pool && L.total > 0)
-        cudaMemcpyAsync(pool, L.pool, (size_t)std::min(L.total, L.capacity) * 64 * sizeof(float),
+        cudaMemcpyAsync(pool, L.pool, (size_t)std::min(L.total, L.capacity) * 64 * g->esize,
                         cudaMemcpyDeviceToDevice, g->stream);
     cudaStreamSynchronize(g->stream);
     g->release(L.pool);
@@ -600,9 +656,20 @@ void launch_pack_keep(Grid* g, Layout& next, StepCounters* ctr)
     const GridGeom& G = g->geom;
     int64_t cps = (G.RW + kPackThreads - 1) / kPackThreads;
     cudaMemsetAsync(next.kcnt, 0, (size_t)G.nb * 4, g->stream);
-    k_pack_keep<<<(unsigned)(cps * G.nb), kPackThreads, 0, g->stream>>>(
-        G, next.view(), next.keepq, next.kbits, next.kcnt, ctr, cps); note_launch();
+    with_codec(g->codec, [&](auto c) {
+        k_pack_keep<decltype(c)::value><<<(unsigned)(cps * G.nb), kPackThreads, 0, g->stream>>>(
+            G, next.view(), next.keepq, next.kbits, next.kcnt, ctr, cps);
+    });
+    note_launch();
     k_dense_k<<<nblk(G.nb, 256), 256, 0, g->stream>>>(next.kcnt, next.dense, G.nb, G.N, G.abort, ctr);
+    note_launch();
+}
+
+void launch_out_scale(Grid* g, const Layout& cur, Layout& next)
+{
+    if (g->codec == 0) return;
+    const GridGeom& G = g->geom;
+    k_out_scale<<<nblk(G.nb, 256), 256, 0, g->stream>>>(cur.vmax, next.scale, next.vmax, G.nb, G.abort);
     note_launch();
 }
 
@@ -628,7 +695,8 @@ struct Scratch {
 }  // namespace
 
 vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* ids_in,
-                     const float* vals_in, int on_device)
+                     const float* vals_in, int on_device, const float* scale_host,
+                     const unsigned* vmax_host)
 {
     const GridGeom& G = g->geom;
     cudaStream_t s = g->stream;
@@ -672,19 +740,41 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     k_dense_k<<<nblk(G.nb, 256), 256, 0, s>>>(L.cnt, L.dense, G.nb, G.N, nullptr, nullptr); note_launch();
     st = layout_ensure_pool(g, L, std::max<int64_t>(M, 1));
     if (st != VL_OK) return st;
-    if (M > 0 && on_device) {
-        k_scatter<<<nblk(M * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, vals, 0, M);
+    // 16-bit storage: the scale of each block id (largest |f| of the input) comes first,
+    // unless given
+    cudaMemsetAsync(L.vmax, 0, (size_t)G.nb * 4, s);
+    const bool given = scale_host && vmax_host;
+    if (given) {
+        cudaMemcpyAsync(L.scale, scale_host, (size_t)G.nb * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(L.vmax, vmax_host, (size_t)G.nb * 4, cudaMemcpyHostToDevice, s);
+    } else if (g->codec == 0) {
+        k_fill_f32<<<nblk(G.nb, 256), 256, 0, s>>>(L.scale, 1.0f, G.nb);
         note_launch();
-    } else if (M > 0) {
-        // host values: copied and scattered in chunks, so the device never holds a second
-        // full copy of the state
-        const int64_t chunk = std::min<int64_t>(M, (int64_t)1 << 22);  // 1 GiB of values
-        float* stage_buf = (float*)sc.get((size_t)chunk * 256);
+    }
+    const int64_t chunk = std::min<int64_t>(std::max<int64_t>(M, 1), (int64_t)1 << 22);  // 1 GiB of values
+    float* stage_buf = nullptr;
+    if (M > 0 && !on_device) {
+        // host values: copied in chunks, so the device never holds a second full copy
+        stage_buf = (float*)sc.get((size_t)chunk * 256);
         if (!stage_buf) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
-        for (int64_t t0 = 0; t0 < M; t0 += chunk) {
-            const int64_t m = std::min(chunk, M - t0);
-            cudaMemcpyAsync(stage_buf, vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice, s);
-            k_scatter<<<nblk(m * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, stage_buf, t0, m);
+    }
+    for (int pass = (g->codec && !given ? 0 : 1); pass < 2 && M > 0; pass++) {
+        for (int64_t t0 = 0; t0 < M; t0 += (on_device ? M : chunk)) {
+            const int64_t m = on_device ? M : std::min(chunk, M - t0);
+            const float* v = on_device ? vals : stage_buf;
+            if (!on_device)
+                cudaMemcpyAsync(stage_buf, vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice, s);
+            if (pass == 0) {
+                k_block_vmax<<<nblk(m * 32, 256), 256, 0, s>>>(ids, v, t0, m, L.vmax);
+            } else {
+                with_codec(g->codec, [&](auto c) {
+                    k_scatter<decltype(c)::value><<<nblk(m * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, v, t0, m);
+                });
+            }
+            note_launch();
+        }
+        if (pass == 0) {
+            k_scale_from_vmax<<<nblk(G.nb, 256), 256, 0, s>>>(L.vmax, L.scale, G.nb);
             note_launch();
         }
     }
@@ -751,7 +841,12 @@ vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capaci
     if (!rank_of || !d_off || !d_ids || !d_vals) return fail(g, VL_ENOMEM, "vl_get_blocks: scratch allocation failed");
     k_offsets64<<<nblk(Wn.ncell + 1, 256), 256, 0, s>>>(cexc, cbase, chunk, Wn.ncell, d_off); note_launch();
     k_fill_ids<<<nblk(Wn.ncell, 128), 128, 0, s>>>(G, Wn, L.view(), d_off, d_ids, rank_of); note_launch();
-    if (M > 0) { k_gather<<<nblk(M * 64, 256), 256, 0, s>>>(L.view(), d_ids, rank_of, d_vals, M); note_launch(); }
+    if (M > 0) {
+        with_codec(g->codec, [&](auto c) {
+            k_gather<decltype(c)::value><<<nblk(M * 64, 256), 256, 0, s>>>(L.view(), d_ids, rank_of, d_vals, M);
+        });
+        note_launch();
+    }
     if (!on_device) {
         cudaMemcpyAsync(off_out, d_off, (size_t)(Wn.ncell + 1) * 8, cudaMemcpyDeviceToHost, s);
         if (M > 0) {
@@ -789,7 +884,10 @@ vl_status moments(Grid* g, double* out, int on_device)
         V.vmin[d] = g->vmesh.vmin[d];
         V.dv[d] = g->vmesh.dv[d];
     }
-    k_moments<<<nblk(G.N * 32, 256), 256, 0, g->stream>>>(G, L.view(), V, d_out); note_launch();
+    with_codec(g->codec, [&](auto c) {
+        k_moments<decltype(c)::value><<<nblk(G.N * 32, 256), 256, 0, g->stream>>>(G, L.view(), V, d_out);
+    });
+    note_launch();
     if (!on_device)
         cudaMemcpyAsync(out, d_out, (size_t)G.N * 7 * 8, cudaMemcpyDeviceToHost, g->stream);
     cudaError_t e = cudaStreamSynchronize(g->stream);

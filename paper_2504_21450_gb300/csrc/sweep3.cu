@@ -55,9 +55,11 @@ __device__ __forceinline__ void pencil_cell(const GridGeom& G, int dim, int64_t 
     }
 }
 
-template <bool kLim>
+template <bool kLim, int kCodec>
 __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
 {
+    using C = Codec<kCodec>;
+    using T = typename C::T;
     __shared__ int s_rin[kPencils][kMaxLine];
     __shared__ int s_rout[kPencils][kMaxLine];
     __shared__ int s_any[kPencils];
@@ -101,8 +103,14 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     // the warp's velocity cells move the same way unless the block straddles v_d = 0
     const bool uni = __all_sync(0xffffffffu, up) || __all_sync(0xffffffffu, !up);
 
-    const float* src = P.in.pool + ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + l;
-    float* dst = P.out.pool + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + l;
+    const T* src = static_cast<const T*>(P.in.pool) +
+                   ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + l;
+    T* dst = static_cast<T*>(P.out.pool) + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + l;
+    // 16-bit storage: scales of the codes read and written (passes 2 and 3 read the
+    // codes the previous pass wrote with the output scale)
+    const float sc_in = kCodec ? P.in.scale[b] : 1.0f;
+    const float sc_out = kCodec ? P.out.scale[b] : 1.0f;
+    const float inv_out = 1.0f / sc_out;  // a power of two: exact
     const int* rin = s_rin[k];
     const int* rout = s_rout[k];
     // the walk runs from the upwind end: walking position m is cell m (c >= 0) or
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     auto cell_at = [&](int m) { return up ? m : nd - 1 - m; };
     auto load = [&](int m) -> float {
         int r = rin[cell_at(m)];
-        return r >= 0 ? src[(int64_t)r * kChunk] : 0.0f;
+        return r >= 0 ? C::dec(src[(int64_t)r * kChunk], sc_in) : 0.0f;
     };
     // originals of walking positions 0 and 1, read again by the wrapped tail after
     // they were updated in place
@@ -119,12 +127,15 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     Walk<kLim> s;
     s.reset();
     float msum = 0.0f;
+    float vmx = 0.0f;  // largest |stored value| (16-bit storage, last pass)
     double mass = 0.0;
     const float thr = P.thr;
     auto emit = [&](int mm, float res) {  // new average of walking position mm
         int c = cell_at(mm);
         int r = rout[c];
-        if (r >= 0) dst[(int64_t)r * kChunk] = res;
+        const T code = C::enc(res, inv_out);
+        if (kCodec) res = C::dec(code, sc_out);  // the value the state now holds
+        if (r >= 0) dst[(int64_t)r * kChunk] = code;
         if (P.last) {
             bool keep = r >= 0 && res >= thr;
             uint8_t* kq = P.keepq + ((int64_t)P.out.base[b] + r) * 4 + q;
@@ -135,7 +146,10 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
             } else if (keep) {
                 *kq = 1;
             }
-            if (r >= 0) msum += res;
+            if (r >= 0) {
+                msum += res;
+                if (kCodec) vmx = fmaxf(vmx, fabsf(res));
+            }
         }
     };
     int m = -3;
@@ -169,6 +183,10 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
         mass += (double)msum;
         for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
         if ((threadIdx.x & 31) == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
+        if (kCodec) {
+            unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
+            if ((threadIdx.x & 31) == 0 && u) atomicMax(&P.out.vmax[b], u);
+        }
     }
 }
 
@@ -202,12 +220,12 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         P.groups = (npen + kPencils - 1) / kPencils;
         int64_t nblocks = P.groups * G.nb;
         if (nblocks > 0x7fffffffLL) return fail(g, VL_EINVAL, "3-pass form: grid too large");
-        if (a.limiter) {
-            k_pass<true><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P); note_launch();
-        }
-        else {
-            k_pass<false><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P); note_launch();
-        }
+        with_codec(g->codec, [&](auto c) {
+            constexpr int kc = decltype(c)::value;
+            if (a.limiter) k_pass<true, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
+            else k_pass<false, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
+        });
+        note_launch();
     }
     record_sweep_event(a.ev1, g->stream, a.ev_node);
     cudaError_t e = cudaGetLastError();
