@@ -232,6 +232,40 @@ def generate_host(cfg, device, slab=2):
     return off, ids_h, vals_h, thr
 
 
+PRESIZE_EDGE = 8       # cost-model tiles: 8^3 cells
+PRESIZE_MARGIN = 0.05  # capacity = (1 + margin) x the summed tile predictions
+
+
+def train_cost_model(horizon, local):
+    """The pre-sizing model, trained with seed 0 on solver traces of the uniform and
+    shock workloads (windows: their full sizes do not fit beside the timed state)."""
+    import torch
+    from paper_2504_21450_gb300 import costmodel, vlasov
+    X_l, T_l, info = [], [], []
+    for name, size, nsteps in (("uniform", (32, 32, 16), horizon + 8), ("shock", (128, 32, 16), horizon + 40)):
+        cfg = inputs.CONFIGS[name]
+        off, ids, vals, thr = inputs.generate_torch(cfg, f"cuda:{local}", size=size)
+        g = vlasov.Grid(size, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, device=local)
+        g.set_blocks(off, ids, vals)
+        del off, ids, vals
+        tr = costmodel.record_run(g, cfg.dt, nsteps, edge=PRESIZE_EDGE)
+        X, T = tr.dataset(horizon)
+        g.close()
+        del tr
+        X_l.append(X)
+        T_l.append(T)
+        info.append(f"{name} {size[0]}x{size[1]}x{size[2]} cells, {nsteps} steps")
+        torch.cuda.empty_cache()
+    X, T = torch.cat(X_l), torch.cat(T_l)
+    model = costmodel.CostModel(seed=0)
+    epochs = 3000
+    t0 = time.perf_counter()
+    losses = model.train(X, T, epochs, lr=3e-3)
+    return model, {"traces": "; ".join(info), "samples": int(X.shape[0]), "epochs": epochs,
+                   "loss_first": losses[0], "loss_last": losses[-1],
+                   "train_s": round(time.perf_counter() - t0, 3)}
+
+
 def run_ours(args, cfg):
     import torch
     from paper_2504_21450_gb300 import vlasov
@@ -247,6 +281,9 @@ def run_ours(args, cfg):
     storage = {"f32": vlasov.VL_STORE_F32, "bf16": vlasov.VL_STORE_BF16_SCALED,
                "f16": vlasov.VL_STORE_F16_SCALED}[args.storage]
 
+    model, train_info = None, None
+    if args.presize == "mlp":
+        model, train_info = train_cost_model(args.chunk or args.steps, local)
     host = None
     e2e_note = None
     big = state_bytes(cfg) > 40e9
@@ -267,14 +304,37 @@ def run_ours(args, cfg):
         del off, ids, vals
     torch.cuda.empty_cache()
 
-    cap = int(g.block_count() * 1.08) if args.graph else 0
-    step_calls = [args.steps] if args.graph else [1] * args.steps
+    chunk = args.chunk or args.steps
+    cap = int(g.block_count() * 1.08) if (args.graph and args.presize == "fixed") else 0
+    step_calls = [chunk] * (args.steps // chunk) + ([args.steps % chunk] if args.steps % chunk else []) \
+        if args.graph else [1] * args.steps
+    caps = []   # capacity asked for per captured call
+    held = []   # blocks the pools held after it
+    unions = []  # union blocks of its last step
+    cap_ms = []  # host time of the capacity decision (features + model) per call
+
+    def capacity_for_call():
+        """Pool capacity of the next captured call: fixed (1.08 x the blocks present),
+        exact (0: the library's default, the last union's exact count + 25%), or the
+        learned model's prediction for the next `chunk` steps."""
+        t0 = time.perf_counter()
+        if args.presize == "mlp":
+            c = model.capacity(g.tile_features(PRESIZE_EDGE)[0], PRESIZE_MARGIN)
+        else:
+            c = cap
+        cap_ms.append(round((time.perf_counter() - t0) * 1e3, 3))
+        caps.append(c)
+        return c
+
     if args.graph:
         # warm-up with the same step count, so that the timed call replays a cached graph
-        g.translate(cfg.dt, args.order, args.steps, form, graph=True, capacity=cap)
-        cap = max(cap, g.stats().capacity)
+        g.translate(cfg.dt, args.order, chunk, form, graph=True, capacity=capacity_for_call())
+        if args.presize == "fixed":
+            cap = max(cap, g.stats().capacity)
         for _ in range(max(0, args.warmup - 1)):
             g.translate(cfg.dt, args.order, 1, form)
+        caps.clear()
+        cap_ms.clear()
     else:
         for _ in range(args.warmup):
             g.translate(cfg.dt, args.order, 1, form)
@@ -287,17 +347,22 @@ def run_ours(args, cfg):
     sweep_ms = 0.0
     launches = 0
     regrows = 0
+    replays = 0
     phases = {"index_ms": 0.0, "sweep_ms": 0.0, "prune_ms": 0.0}
     stats = None
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for n in step_calls:
-            g.translate(cfg.dt, args.order, n, form, graph=args.graph, capacity=cap)
+            g.translate(cfg.dt, args.order, n, form, graph=args.graph,
+                        capacity=capacity_for_call() if args.graph else 0)
             s = g.stats()
             updates += s.updates
             sweep_ms += s.sweep_ms
             launches += s.launches
             regrows += s.capacity_regrows
+            replays += s.graph_replays
+            held.append(int(s.capacity))
+            unions.append(int(s.union_blocks))
             stats = s
             for k in phases:
                 phases[k] += getattr(s, k)
@@ -370,6 +435,11 @@ def run_ours(args, cfg):
                    "l2": f"state ({updates / args.steps * STORAGE_BYTES[args.storage] / 1e9:.1f} GB per copy) larger than L2; no flush",
                    "blocks_per_step": updates / args.steps / 64},
         "roofline": roofline,
+        **({"presize": {"mode": args.presize, "chunk": chunk, "capacity_blocks": caps,
+                        "held_blocks": held, "union_blocks_at_end": unions, "decision_ms": cap_ms,
+                        "blocks_present_last": int(stats.blocks), "union_blocks_last": int(stats.union_blocks),
+                        "capacity_regrows": regrows, "graph_replays": replays, "train": train_info}}
+           if args.graph else {}),
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -400,6 +470,10 @@ def main():
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="override the spatial extent (smaller cases for profiling)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--presize", default="fixed", choices=["fixed", "exact", "mlp"],
+                    help="pool capacity of captured calls: 1.08 x blocks present, the last exact "
+                         "union count + 25%%, or the learned cost model")
+    ap.add_argument("--chunk", type=int, default=0, help="steps per captured call (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     cfg = inputs.CONFIGS[args.config]

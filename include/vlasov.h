@@ -259,6 +259,71 @@ vl_status vl_translate_dense_noalloc(const vl_space_desc* space, const vl_vmesh_
                                      const float* f_in, float* f_out, double* mass_out,
                                      void* stream);
 
+/* ---- learned cost model --------------------------------------------------------------
+ * The paper weighs each spatial cell by the complexity of its velocity space when it
+ * balances load (Section 2) and notes that ghost cells change that cost (Section 5).
+ * These calls predict the same quantity ahead of time: for a tile of edge^3 cells, the
+ * blocks it will hold over the next steps.  Summed over tiles, the prediction sizes
+ * the block pools of a captured step sequence (vl_translate_opts.capacity).  Nothing
+ * here reads or writes f.
+ *
+ * Tiles: edge^3 cells (the last tile of a dimension may be shorter), numbered x
+ * fastest; vl_tile_count gives their number (-1 for bad arguments).
+ *
+ * vl_tile_features writes, per tile, VL_MLP_NIN float32 features (device buffer
+ * [ntiles][VL_MLP_NIN]): log(1+A), log(1+U), log(1+mean n), mean V_x, mean V_y, mean V_z,
+ * mean v_th, max |grad n| / n, where A = blocks present in the tile, U = blocks of the
+ * tile in the next step's 27-cell union, n, V and v_th = sqrt((Pxx+Pyy+Pzz)/(3n)) are the
+ * per-cell moments of vl_moments (V and v_th taken as 0 where n = 0), means over the
+ * tile's cells, and grad n by periodic central differences.  union_blocks (device
+ * [ntiles]) receives U.  Synchronises the grid's stream; needs a state (VL_ESTATE).
+ * Errors: VL_EINVAL (edge outside 1..64, null pointer), VL_ENOMEM, VL_ECUDA.
+ *
+ * vl_cost_targets: from union_trace (device [nsnap][ntiles], U of consecutive states)
+ * the regression targets targets[t][i] = log(1 + max_{0<=j<horizon} U[t+j][i]) for
+ * t = 0 .. nsnap-horizon (device).  Errors: VL_EINVAL (nsnap < horizon, horizon < 1).
+ *
+ * The model: y = b3 + w3 . relu(W2 relu(W1 x + b1) + b2), float32, parameters in one
+ * device array of VL_MLP_NPARAM floats laid out W1[64][8] (row = hidden unit), b1[64],
+ * W2[64][64], b2[64], w3[64], b3.  Loss L = (1/n) sum_s (y_s - t_s)^2.
+ * vl_mlp_forward: y[s] for n samples x[n][8] (device).
+ * vl_mlp_gradient: dL/dparams into grad (device, VL_MLP_NPARAM) and L into *loss
+ *   (device double), sums over samples in a fixed order in FP64 (reproducible).
+ * vl_mlp_train_step: one full-batch Adam step (beta1 VL_MLP_BETA1, beta2 VL_MLP_BETA2,
+ *   eps VL_MLP_EPS, bias-corrected; step counts from 1) on params with the moment
+ *   arrays adam_m, adam_v (device, VL_MLP_NPARAM each, zero before step 1); *loss
+ *   (device, optional) receives L before the update.
+ * Both take a caller-provided device workspace, 256-byte aligned, of at least
+ * vl_mlp_workspace_bytes(n) bytes, and allocate nothing.
+ * vl_mlp_capacity: ceil((1 + margin) * sum_i max(exp(y_i) - 1, 0)) over the tiles'
+ *   predictions into *capacity (host); workspace of at least 256*ceil(4*ntiles/256) + 8
+ *   bytes.  Synchronises `stream`.
+ * All calls queue work on `stream` (cudaStream_t of the current device; NULL = legacy
+ * default stream).  Errors: VL_EINVAL (null pointer, n < 0, small or misaligned
+ * workspace, step < 1), VL_ECUDA. */
+#define VL_MLP_NIN 8
+#define VL_MLP_NHIDDEN 64
+#define VL_MLP_NPARAM \
+    (VL_MLP_NHIDDEN * VL_MLP_NIN + VL_MLP_NHIDDEN * VL_MLP_NHIDDEN + 3 * VL_MLP_NHIDDEN + 1) /* 4801 */
+#define VL_MLP_BETA1 0.9f
+#define VL_MLP_BETA2 0.999f
+#define VL_MLP_EPS 1e-8f
+int64_t vl_tile_count(const vl_space_desc* space, int edge);
+vl_status vl_tile_features(vl_grid* grid, int edge, float* features, float* union_blocks);
+vl_status vl_cost_targets(const float* union_trace, int nsnap, int64_t ntiles, int horizon,
+                          float* targets, void* stream);
+vl_status vl_mlp_forward(const float* params, const float* x, int64_t n, float* y, void* stream);
+size_t vl_mlp_workspace_bytes(int64_t n);
+vl_status vl_mlp_gradient(const float* params, const float* x, const float* t, int64_t n,
+                          void* workspace, size_t workspace_bytes, float* grad, double* loss,
+                          void* stream);
+vl_status vl_mlp_train_step(float* params, float* adam_m, float* adam_v, const float* x,
+                            const float* t, int64_t n, int step, float lr, void* workspace,
+                            size_t workspace_bytes, double* loss, void* stream);
+vl_status vl_mlp_capacity(const float* params, const float* features, int64_t ntiles,
+                          double margin, void* workspace, size_t workspace_bytes,
+                          int64_t* capacity, void* stream);
+
 const char* vl_status_str(vl_status status);
 const char* vl_last_error(const vl_grid* grid);
 

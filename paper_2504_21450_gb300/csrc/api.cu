@@ -243,9 +243,12 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
             else g->graph_ev.push_back(ev);
         }
         if (st != VL_OK) break;
+        // the captured steps check the union against what the pools hold, which is at
+        // least `cap`: a later call asking for less replays the same graph
+        const int64_t held = std::min(g->lay[0].capacity, g->lay[1].capacity);
         uint64_t key = 0;
         const uint64_t parts[] = {(uint64_t)n, (uint64_t)fused, (uint64_t)a.limiter, (uint64_t)a.order[0],
-                                  (uint64_t)a.order[1], (uint64_t)a.order[2], (uint64_t)cap, (uint64_t)g->cur,
+                                  (uint64_t)a.order[1], (uint64_t)a.order[2], (uint64_t)held, (uint64_t)g->cur,
                                   (uint64_t)(uintptr_t)g->lay[0].pool, (uint64_t)(uintptr_t)g->lay[1].pool,
                                   (uint64_t)(uintptr_t)g->step_ctr, (uint64_t)(uintptr_t)g->items,
                                   (uint64_t)(uintptr_t)a.walk, (uint64_t)(uintptr_t)g->stream,
@@ -270,7 +273,7 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
                 ak.ev0 = g->graph_ev[2 * k];
                 ak.ev1 = g->graph_ev[2 * k + 1];
                 ak.ev_node = true;
-                st = enqueue_step(g, ak, fused, true, cap, g->step_ctr + k);
+                st = enqueue_step(g, ak, fused, true, held, g->step_ctr + k);
                 g->cur = 1 - g->cur;
             }
             cudaGraph_t graph = nullptr;
@@ -328,7 +331,7 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
             }
         }
     }
-    S->capacity = cap;
+    S->capacity = std::min(g->lay[0].capacity, g->lay[1].capacity);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
@@ -714,6 +717,14 @@ vl_status vl_moments(vl_grid* grid, double* out, int on_device)
     Grid* g = reinterpret_cast<Grid*>(grid);
     DeviceGuard dg(g->dev.device);
     return moments(g, out, on_device);
+}
+
+vl_status vl_tile_features(vl_grid* grid, int edge, float* features, float* union_blocks)
+{
+    if (!grid) return VL_EINVAL;
+    Grid* g = reinterpret_cast<Grid*>(grid);
+    DeviceGuard dg(g->dev.device);
+    return tile_features(g, edge, features, union_blocks);
 }
 
 vl_status vl_mass(vl_grid* grid, double* mass)

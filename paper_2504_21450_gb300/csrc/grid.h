@@ -125,6 +125,7 @@ vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capaci
                      int64_t* off_out, uint16_t* ids_out, float* vals_out, int on_device,
                      int64_t* count);
 vl_status moments(Grid* g, double* out, int on_device);
+vl_status tile_features(Grid* g, int edge, float* feat, float* uni);
 vl_status total_mass(Grid* g, double* mass);
 // Generic scans used by the layout code and the work lists.
 void launch_seg_scan(const uint32_t* in, uint32_t* out, uint32_t* seg_total, int64_t seg_len,

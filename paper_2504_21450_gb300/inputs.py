@@ -285,3 +285,18 @@ def generate_torch(cfg: Config, device, origin=(0, 0, 0), size=None, thr: float 
     ids = torch.cat(parts_ids) if parts_ids else torch.zeros(0, dtype=torch.int32, device=device)
     vals = torch.cat(parts_vals) if parts_vals else torch.zeros((0, 64), dtype=torch.float32, device=device)
     return off, ids, vals, thr
+
+
+def mlp_init(seed: int = 0, nin: int = 8, nh: int = 64) -> np.ndarray:
+    """Initial parameters of the cost model's MLP (flat float32, layout W1[nh][nin], b1,
+    W2[nh][nh], b2, w3, b3): weights uniform in +-sqrt(6 / (fan_in + fan_out)) (Glorot
+    and Bengio 2010), biases 0, from numpy's PCG64 with the given seed."""
+    rng = np.random.default_rng(seed)
+
+    def glorot(fan_out, fan_in):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(-lim, lim, (fan_out, fan_in))
+
+    parts = [glorot(nh, nin).ravel(), np.zeros(nh), glorot(nh, nh).ravel(), np.zeros(nh),
+             glorot(1, nh).ravel(), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

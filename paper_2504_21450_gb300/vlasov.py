@@ -98,6 +98,14 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "vl_import": (i, [p, p, ctypes.c_size_t]),
         "vl_status_str": (ctypes.c_char_p, [i]),
         "vl_last_error": (ctypes.c_char_p, [p]),
+        "vl_tile_count": (i64, [p, i]),
+        "vl_tile_features": (i, [p, i, p, p]),
+        "vl_cost_targets": (i, [p, i, i64, i, p, p]),
+        "vl_mlp_forward": (i, [p, p, i64, p, p]),
+        "vl_mlp_workspace_bytes": (ctypes.c_size_t, [i64]),
+        "vl_mlp_gradient": (i, [p, p, p, i64, p, ctypes.c_size_t, p, p, p]),
+        "vl_mlp_train_step": (i, [p, p, p, p, p, i64, i, ctypes.c_float, p, ctypes.c_size_t, p, p]),
+        "vl_mlp_capacity": (i, [p, p, i64, d, p, ctypes.c_size_t, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -205,6 +213,51 @@ def vl_translate_dense_noalloc(space: vl_space_desc, vmesh: vl_vmesh_desc, dt: f
                                              mass_out_ptr, stream_ptr)
 
 
+# Learned cost model (device pointers as ints, streams as cudaStream_t ints) ----------
+VL_MLP_NIN, VL_MLP_NHIDDEN = 8, 64
+VL_MLP_NPARAM = VL_MLP_NHIDDEN * VL_MLP_NIN + VL_MLP_NHIDDEN * VL_MLP_NHIDDEN + 3 * VL_MLP_NHIDDEN + 1
+
+
+def vl_tile_count(space: vl_space_desc, edge: int) -> int:
+    return int(load().vl_tile_count(ctypes.byref(space), int(edge)))
+
+
+def vl_tile_features(grid, edge: int, features_ptr: int, union_ptr: int) -> None:
+    _check(load().vl_tile_features(grid, int(edge), features_ptr, union_ptr), "vl_tile_features", grid)
+
+
+def vl_cost_targets(trace_ptr: int, nsnap: int, ntiles: int, horizon: int, targets_ptr: int,
+                    stream_ptr: int) -> None:
+    _check(load().vl_cost_targets(trace_ptr, int(nsnap), int(ntiles), int(horizon), targets_ptr,
+                                  stream_ptr), "vl_cost_targets")
+
+
+def vl_mlp_forward(params_ptr: int, x_ptr: int, n: int, y_ptr: int, stream_ptr: int) -> None:
+    _check(load().vl_mlp_forward(params_ptr, x_ptr, int(n), y_ptr, stream_ptr), "vl_mlp_forward")
+
+
+def vl_mlp_workspace_bytes(n: int) -> int:
+    return int(load().vl_mlp_workspace_bytes(int(n)))
+
+
+def vl_mlp_gradient(params_ptr, x_ptr, t_ptr, n, ws_ptr, ws_bytes, grad_ptr, loss_ptr, stream_ptr) -> None:
+    _check(load().vl_mlp_gradient(params_ptr, x_ptr, t_ptr, int(n), ws_ptr, int(ws_bytes), grad_ptr,
+                                  loss_ptr, stream_ptr), "vl_mlp_gradient")
+
+
+def vl_mlp_train_step(params_ptr, m_ptr, v_ptr, x_ptr, t_ptr, n, step, lr, ws_ptr, ws_bytes,
+                      loss_ptr, stream_ptr) -> None:
+    _check(load().vl_mlp_train_step(params_ptr, m_ptr, v_ptr, x_ptr, t_ptr, int(n), int(step), float(lr),
+                                    ws_ptr, int(ws_bytes), loss_ptr, stream_ptr), "vl_mlp_train_step")
+
+
+def vl_mlp_capacity(params_ptr, features_ptr, ntiles, margin, ws_ptr, ws_bytes, stream_ptr) -> int:
+    out = ctypes.c_int64()
+    _check(load().vl_mlp_capacity(params_ptr, features_ptr, int(ntiles), float(margin), ws_ptr,
+                                  int(ws_bytes), ctypes.byref(out), stream_ptr), "vl_mlp_capacity")
+    return int(out.value)
+
+
 # Convenience object -------------------------------------------------------------------
 class Grid:
     """One phase-space grid on the current CUDA device, memory from PyTorch's allocator."""
@@ -244,6 +297,7 @@ class Grid:
                               (ctypes.c_double * 3)(0.0, 0.0, 0.0))
         vm = vl_vmesh_desc((ctypes.c_int * 3)(*self.nv), (ctypes.c_double * 3)(*self.vmin),
                            (ctypes.c_double * 3)(*self.dv), (ctypes.c_int * 3)(4, 4, 4))
+        self.space = space
         self.handle = vl_grid_create(space, vm, threshold, storage, self._dev)
 
     def close(self):
@@ -327,6 +381,15 @@ class Grid:
 
     def mass(self) -> float:
         return vl_mass(self.handle)
+
+    def tile_features(self, edge: int = 8):
+        """(features [ntiles][8], union blocks [ntiles]) as CUDA tensors."""
+        t = self.torch
+        nt = vl_tile_count(self.space, edge)
+        f = t.empty((nt, VL_MLP_NIN), dtype=t.float32, device=self.device)
+        u = t.empty(nt, dtype=t.float32, device=self.device)
+        vl_tile_features(self.handle, edge, f.data_ptr(), u.data_ptr())
+        return f, u
 
     def stats(self) -> vl_step_stats:
         return vl_stats(self.handle)

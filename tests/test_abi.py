@@ -58,3 +58,25 @@ def test_host_side_argument_checks(lib):
     assert L.vl_grid_create(None, None, 0.0, 0, None, ctypes.byref(g)) == vlasov.VL_EINVAL
     assert L.vl_translate(None, 0.1, b"xyz", 1, None) == vlasov.VL_EINVAL
     assert L.vl_grid_destroy(None) == vlasov.VL_OK
+
+
+def test_cost_model_host_side_checks(lib):
+    """Argument checks and sizes of the cost-model entry points (no device work)."""
+    from paper_2504_21450_gb300 import vlasov
+    L = vlasov.load()
+    space = vlasov.vl_space_desc((ctypes.c_int * 3)(19, 13, 10), (ctypes.c_double * 3)(1, 1, 1),
+                                 (ctypes.c_double * 3)(0, 0, 0))
+    assert vlasov.vl_tile_count(space, 8) == 3 * 2 * 2
+    assert vlasov.vl_tile_count(space, 0) == -1
+    assert vlasov.VL_MLP_NPARAM == 4801
+    assert vlasov.vl_mlp_workspace_bytes(1000) >= 1000 * (4 * 64 * 4 + 8) + 4801 * 4
+    assert L.vl_mlp_forward(None, None, 5, None, None) == vlasov.VL_EINVAL
+    assert L.vl_mlp_forward(ctypes.c_void_p(256), None, 0, None, None) == vlasov.VL_OK  # nothing to do
+    assert L.vl_cost_targets(ctypes.c_void_p(256), 3, 10, 4, ctypes.c_void_p(512), None) == vlasov.VL_EINVAL
+    ws = ctypes.c_void_p(1 << 20)
+    assert L.vl_mlp_train_step(ws, ws, ws, ws, ws, 10, 0, 1e-3, ws, 1 << 20, None, None) == vlasov.VL_EINVAL
+    assert L.vl_mlp_train_step(ws, ws, ws, ws, ws, 10, 1, 1e-3, ctypes.c_void_p((1 << 20) + 8), 1 << 20,
+                               None, None) == vlasov.VL_EINVAL  # misaligned workspace
+    out = ctypes.c_int64()
+    assert L.vl_mlp_capacity(ws, ws, 10, -1.0, ws, 1 << 20, ctypes.byref(out), None) == vlasov.VL_EINVAL
+    assert L.vl_tile_features(None, 8, None, None) == vlasov.VL_EINVAL

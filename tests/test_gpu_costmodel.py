@@ -1,0 +1,179 @@
+"""The learned cost model on the GPU: tile features, MLP forward / gradient / Adam,
+targets and capacity against the FP64 oracle (oracle/mlp.py); training on solver traces
+is reproducible and lowers the loss; pre-sized captured runs leave f unchanged."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2504_21450_gb300 import costmodel, inputs, vlasov
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    vlasov.load(build_if_missing=True)
+
+
+def stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def smooth_sparse_case(seed, n=(19, 13, 10)):
+    """Random block sets with a smooth density modulation per cell (so that the
+    gradient feature is not noise only)."""
+    init = inputs.random_blocks(n, (8, 8, 8), 0.3, seed=seed)
+    cell = np.repeat(np.arange(int(np.prod(n))), np.diff(init.off))
+    x = cell % n[0]
+    w = (1.0 + 0.5 * np.sin(2 * np.pi * x / n[0])).astype(np.float32)
+    vals = (init.vals * w[:, None]).astype(np.float32)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0, -3.0, -4.5), dv=(1.0,) * 3)
+    return init.off, init.ids, vals, mesh
+
+
+@pytest.mark.parametrize("edge", [4, 8])
+def test_tile_features_match_the_oracle(edge):
+    off, ids, vals, mesh = smooth_sparse_case(90)
+    g = vlasov.Grid(mesh.n, mesh.nv, mesh.vmin, mesh.dv, mesh.dx, threshold=0.05)
+    g.set_blocks(off, ids, vals)
+    f, u = g.tile_features(edge)
+    F, U = omlp.tile_features(mesh, oracle.as_blocks(off, ids, vals.astype(np.float64)), edge)
+    np.testing.assert_array_equal(u.cpu().numpy(), U.astype(np.float32))  # integer counts
+    # moments from FP32 sums per block (about the block's velocity centre), FP64 per cell
+    np.testing.assert_allclose(f.cpu().numpy(), F, rtol=1e-5, atol=1e-6)
+    # the features leave the state alone: a step afterwards equals a step without them
+    g.translate(0.2, "xyz", 1, check=True)
+    h = vlasov.Grid(mesh.n, mesh.nv, mesh.vmin, mesh.dv, mesh.dx, threshold=0.05)
+    h.set_blocks(off, ids, vals)
+    h.translate(0.2, "xyz", 1, check=True)
+    for a, b in zip(g.get_blocks(), h.get_blocks()):
+        np.testing.assert_array_equal(a, b)
+    g.close()
+    h.close()
+
+
+def mlp_case(n=300, seed=4):
+    import torch
+    rng = np.random.default_rng(seed)
+    p = inputs.mlp_init(seed).astype(np.float64)
+    p[512:576] = rng.normal(0, 0.1, 64)       # b1
+    p[4672:4736] = rng.normal(0, 0.1, 64)     # b2
+    X = rng.normal(0, 1.5, (n, 8))
+    T = rng.normal(0, 1, n)
+    P = torch.tensor(p, dtype=torch.float32, device="cuda")
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    # the oracle works on exactly the float32 values the GPU sees
+    return P, Xd, Td, P.cpu().double().numpy(), Xd.cpu().double().numpy(), Td.cpu().double().numpy()
+
+
+def workspace(n):
+    import torch
+    nbytes = vlasov.vl_mlp_workspace_bytes(n)
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    return buf, base + (-base) % 256, nbytes
+
+
+@pytest.mark.parametrize("n", [1, 127, 300])
+def test_forward_and_gradient_match_the_oracle(n):
+    import torch
+    P, X, T, p, x, t = mlp_case(n)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    vlasov.vl_mlp_forward(P.data_ptr(), X.data_ptr(), n, y.data_ptr(), stream())
+    yo, _ = omlp.forward(p, x)
+    np.testing.assert_allclose(y.cpu().numpy(), yo, rtol=0, atol=1e-5 * max(1.0, np.abs(yo).max()))
+    buf, ws, nbytes = workspace(n)
+    grad = torch.empty_like(P)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    vlasov.vl_mlp_gradient(P.data_ptr(), X.data_ptr(), T.data_ptr(), n, ws, nbytes, grad.data_ptr(),
+                           loss.data_ptr(), stream())
+    go = omlp.gradient(p, x, t)
+    np.testing.assert_allclose(grad.cpu().numpy(), go, rtol=0, atol=1e-5 * np.abs(go).max())
+    assert float(loss) == pytest.approx(omlp.loss(p, x, t), rel=1e-5)
+
+
+def test_adam_steps_match_the_oracle_on_the_gpu_gradient():
+    """The optimizer's arithmetic, isolated: each GPU step against the oracle's Adam
+    applied to the gradient the GPU computed for that step."""
+    import torch
+    P, X, T, p, x, t = mlp_case(200, seed=5)
+    n = 200
+    buf, ws, nbytes = workspace(n)
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    grad = torch.empty_like(P)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    po, mo, vo = P.cpu().double().numpy(), np.zeros(omlp.NPARAM), np.zeros(omlp.NPARAM)
+    for step in range(1, 6):
+        vlasov.vl_mlp_gradient(P.data_ptr(), X.data_ptr(), T.data_ptr(), n, ws, nbytes, grad.data_ptr(),
+                               loss.data_ptr(), stream())
+        g = grad.cpu().double().numpy()
+        vlasov.vl_mlp_train_step(P.data_ptr(), m.data_ptr(), v.data_ptr(), X.data_ptr(), T.data_ptr(), n,
+                                 step, 1e-2, ws, nbytes, loss.data_ptr(), stream())
+        po, mo, vo = omlp.adam_step(po, mo, vo, g, step, 1e-2)
+        np.testing.assert_allclose(P.cpu().numpy(), po, rtol=0, atol=2e-6)
+        po = P.cpu().double().numpy()  # continue from the GPU's parameters
+
+
+def test_targets_and_capacity_match_the_oracle():
+    import torch
+    rng = np.random.default_rng(7)
+    trace = rng.integers(0, 5000, (9, 37)).astype(np.float32)
+    tr = torch.tensor(trace, device="cuda")
+    out = torch.empty((6, 37), dtype=torch.float32, device="cuda")
+    vlasov.vl_cost_targets(tr.data_ptr(), 9, 37, 4, out.data_ptr(), stream())
+    np.testing.assert_allclose(out.cpu().numpy(), omlp.targets(trace, 4), rtol=2e-7)
+    P, X, T, p, x, t = mlp_case(37)
+    buf, ws, nbytes = workspace(37)
+    cap = vlasov.vl_mlp_capacity(P.data_ptr(), X.data_ptr(), 37, 0.05, ws, nbytes, stream())
+    assert abs(cap - omlp.capacity(p, x, 0.05)) <= 1
+
+
+def shock_window_trace(nsteps, horizon):
+    cfg = inputs.CONFIGS["shock"]
+    init = inputs.generate(cfg, origin=(32, 0, 0), size=(64, 16, 8))
+    g = vlasov.Grid(init.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=init.threshold)
+    g.set_blocks(init.off, init.ids, init.vals)
+    tr = costmodel.record_run(g, cfg.dt, nsteps, edge=8)
+    X, T = tr.dataset(horizon)
+    g.close()
+    return X, T
+
+
+def test_training_on_solver_traces_is_reproducible_and_learns():
+    X, T = shock_window_trace(10, 4)
+    a = costmodel.CostModel(seed=0)
+    la = a.train(X, T, 400, lr=3e-3)
+    b = costmodel.CostModel(seed=0)
+    lb = b.train(X, T, 400, lr=3e-3)
+    assert la == lb
+    assert np.array_equal(a.params.cpu().numpy(), b.params.cpu().numpy())
+    assert la[-1] < 0.05 * la[0], (la[0], la[-1])
+
+
+def test_presized_captured_run_is_bit_identical():
+    """The capacity only sizes memory: a captured run with the model's capacity and one
+    with the default (exact count plus slack) produce the same state."""
+    cfg = inputs.CONFIGS["shock"]
+    init = inputs.generate(cfg, origin=(32, 0, 0), size=(64, 16, 8))
+    X, T = shock_window_trace(8, 4)
+    model = costmodel.CostModel(seed=0)
+    model.train(X, T, 300)
+    out = []
+    for presize in (False, True):
+        g = vlasov.Grid(init.n, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=init.threshold)
+        g.set_blocks(init.off, init.ids, init.vals)
+        regrows = 0
+        for _ in range(3):
+            cap = model.capacity(g.tile_features(8)[0], 0.05) if presize else 0
+            g.translate(cfg.dt, "xyz", 4, vlasov.VL_FORM_FUSED, graph=True, capacity=cap, check=True)
+            regrows += g.stats().capacity_regrows
+        out.append(g.get_blocks())
+        g.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
