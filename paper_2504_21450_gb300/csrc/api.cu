@@ -55,6 +55,14 @@ vl_status cuda_fail(Grid* g, cudaError_t e, const char* what)
     return fail(g, VL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+bool fault_requested(const char* what)
+{
+    const char* env = std::getenv("VLGT_FAULT");
+    if (!env || !what || !*what) return false;
+    const std::string list = std::string(",") + env + ",";
+    return list.find(std::string(",") + what + ",") != std::string::npos;
+}
+
 }  // namespace vlgt
 
 using namespace vlgt;

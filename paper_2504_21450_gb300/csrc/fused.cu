@@ -73,6 +73,8 @@ struct FusedArgs {
     const int64_t* item_base;  // [nb + 1]
     uint8_t* keepq;
     StepCounters* ctr;
+    int report_late;     // testing hook: a staging wait that is not complete at its first
+                         // poll is reported as overdue (VL_ETIMEOUT), then waited for
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
@@ -110,6 +112,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ void mbar_add_tx(uint64_t* bar, unsigned bytes)
 {
     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -143,9 +161,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
-// Upper bound on polls of a staging barrier before the kernel gives up: far beyond any
-// real copy time (a plane is a few tens of kB), so reaching it means a fault upstream.
+// Bounds of a staging wait before the kernel gives up and flags VL_ETIMEOUT: one second
+// of device time (a plane is a few tens of kB, staged in microseconds), and a poll count
+// as a second limit.  Reaching either means a fault upstream.
 constexpr unsigned kMaxPolls = 1u << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;
 
 template <int TY, bool kLim, bool kZUni, int kCodec>
 __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
@@ -370,9 +390,11 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             if (bulk || sbulk) {
                 uint64_t* bar = &s_bar[(gstep + s) % NST];
                 const unsigned parity = ((gstep + s) / NST) & 1u;
+                if (P.report_late && !mbar_test_wait(bar, parity)) atomicOr(&P.ctr->error, 4);
                 unsigned polls = 0;
+                const uint64_t t0 = globaltimer_ns();
                 while (!mbar_try_wait(bar, parity)) {
-                    if (++polls > kMaxPolls) {
+                    if (++polls > kMaxPolls || ((polls & 63u) == 0 && globaltimer_ns() - t0 > kWaitNs)) {
                         atomicOr(&P.ctr->error, 4);
                         break;
                     }
@@ -697,6 +719,7 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.item_base = g->item_base;
     P.keepq = B.keepq;
     P.ctr = a.ctr;
+    P.report_late = fault_requested("timeout") ? 1 : 0;
     record_sweep_event(a.ev0, g->stream, a.ev_node);
     vl_status st = VL_OK;
     with_codec(g->codec, [&](auto c) {
@@ -738,6 +761,7 @@ vl_status launch_fused_dense(const GridGeom& G, const LayoutView& in, const Layo
     P.item_base = item_base;
     P.keepq = nullptr;
     P.ctr = ctr;
+    P.report_late = 0;
     Grid tmp;  // launch helper needs the device and the stream only
     tmp.dev.device = device;
     tmp.stream = stream;

@@ -146,6 +146,12 @@ struct StepArgs {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the sweep kernels when set
     bool ev_node = false;  // inside a stream capture: record as event record nodes
 };
+// Host-side fault injection for tests: true when the environment variable VLGT_FAULT
+// lists `what` (comma-separated).  "timeout": the fused kernel reports staging waits
+// that are not complete at their first poll as overdue (VL_ETIMEOUT) -- they still
+// complete, so no copy is left in flight.
+bool fault_requested(const char* what);
+
 // Calls f(std::integral_constant<int, k>{}) for storage codec k (0 float32, 1 bfloat16,
 // 2 float16), so that one launch site instantiates the kernel for every codec.
 template <class F>

@@ -263,7 +263,9 @@ class Grid:
     """One phase-space grid on the current CUDA device, memory from PyTorch's allocator."""
 
     def __init__(self, n, nv, vmin, dv, dx=(1.0, 1.0, 1.0), threshold: float = 0.0,
-                 storage: int = VL_STORE_F32, device: int | None = None):
+                 storage: int = VL_STORE_F32, device: int | None = None, allocator=None):
+        """allocator: optional callable nbytes -> device pointer (int) or None, used in
+        place of PyTorch's caching allocator (its blocks are still freed through it)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libvlgt needs a CUDA device; there is no CPU fallback")
@@ -282,6 +284,8 @@ class Grid:
 
         def _alloc(nbytes, ctx):
             try:
+                if allocator is not None:
+                    return allocator(int(nbytes))
                 return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev_index, stream))
             except Exception:
                 return None
