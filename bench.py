@@ -326,6 +326,15 @@ def run_ours(args, cfg):
         caps.append(c)
         return c
 
+    tune = None
+    if form == vlasov.VL_FORM_AUTO:
+        # the autotuner's probe steps (one warm-up and one timed step per candidate),
+        # before and apart from the warm-up below
+        g.translate(cfg.dt, args.order, 6, form)
+        st = g.stats()
+        tune = {"ms_per_step": dict(zip(["fused16", "fused8", "3pass"], [round(x, 3) for x in st.tune_ms])),
+                "chosen": {vlasov.VL_FORM_FUSED: "fused", vlasov.VL_FORM_3PASS: "3pass"}.get(st.form_used),
+                "tile_rows": int(st.tile_rows_used)}
     if args.graph:
         # warm-up with the same step count, so that the timed call replays a cached graph
         g.translate(cfg.dt, args.order, chunk, form, graph=True, capacity=capacity_for_call())
@@ -435,6 +444,7 @@ def run_ours(args, cfg):
                    "l2": f"state ({updates / args.steps * STORAGE_BYTES[args.storage] / 1e9:.1f} GB per copy) larger than L2; no flush",
                    "blocks_per_step": updates / args.steps / 64},
         "roofline": roofline,
+        **({"autotune": tune} if tune else {}),
         **({"presize": {"mode": args.presize, "chunk": chunk, "capacity_blocks": caps,
                         "held_blocks": held, "union_blocks_at_end": unions, "decision_ms": cap_ms,
                         "blocks_present_last": int(stats.blocks), "union_blocks_last": int(stats.union_blocks),
@@ -460,7 +470,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fused", choices=["fused", "3pass", "auto"])
+    ap.add_argument("--form", default="auto", choices=["fused", "3pass", "auto"],
+                    help="auto: the library's autotuner times the fused form (16- and 8-row "
+                         "tiles) and the 3-pass form on this workload and keeps the fastest")
     ap.add_argument("--graph", action="store_true",
                     help="run the timed steps as one captured CUDA graph (no host sync per step)")
     ap.add_argument("--config", default="uniform", choices=sorted(inputs.CONFIGS))

@@ -351,8 +351,17 @@ struct TuneEntry {
     int ty;
     double ms[3];
 };
+// Probing in progress for a workload key: the next candidate, whether its warm-up step
+// has run, and the results so far.  Calls of a few steps each advance it in turn.
+struct TuneProgress {
+    int cand = 0;
+    bool warmed = false;
+    double best = 1e300;
+    TuneEntry entry{VL_FORM_FUSED, 0, {0.0, 0.0, 0.0}};
+};
 std::mutex g_tune_mu;
 std::map<uint64_t, TuneEntry> g_tune;
+std::map<uint64_t, TuneProgress> g_tune_progress;
 bool g_tune_loaded = false;
 
 uint64_t tune_key(const Grid* g, const StepArgs& a)
@@ -830,22 +839,26 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
         if (!known) {
             const int cand_form[3] = {VL_FORM_FUSED, VL_FORM_FUSED, VL_FORM_3PASS};
             const int cand_ty[3] = {16, 8, 0};
-            double best = 1e300;
-            bool complete = true;
-            for (int c = 0; c < 3 && st == VL_OK; c++) {
-                if (cand_ty[c] == 16 && a.order[2] != 2) continue;  // 16-row tiles need a z-last order
-                // 16-bit storage: the 3-pass form rounds to storage after every sweep, so
-                // it is not the same computation as the fused form; only tile sizes are tuned
-                if (cand_form[c] == VL_FORM_3PASS && g->codec != 0) continue;
-                if (nsteps - done < 2) {
-                    complete = false;
-                    break;
+            TuneProgress pr;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                pr = g_tune_progress[key];
+            }
+            // each candidate: one warm-up step, then one timed step, possibly over
+            // several calls; every step advances the real state
+            while (st == VL_OK && pr.cand < 3 && done < nsteps) {
+                const int c = pr.cand;
+                // 16-row tiles need a z-last order; with 16-bit storage the 3-pass form
+                // rounds to storage after every sweep, so it is not the same computation
+                // as the fused form and only tile sizes are tuned
+                if ((cand_ty[c] == 16 && a.order[2] != 2) || (cand_form[c] == VL_FORM_3PASS && g->codec != 0)) {
+                    pr.cand++;
+                    continue;
                 }
                 StepArgs ac = a;
                 ac.tile[1] = cand_ty[c];
                 vl_step_stats probe{};
-                st = translate_steps(g, ac, cand_form[c] == VL_FORM_FUSED, 1, &S);
-                if (st == VL_OK) st = translate_steps(g, ac, cand_form[c] == VL_FORM_FUSED, 1, &probe);
+                st = translate_steps(g, ac, cand_form[c] == VL_FORM_FUSED, 1, &probe);
                 if (st != VL_OK) break;
                 S.steps += probe.steps;
                 S.device_ms += probe.device_ms;
@@ -858,22 +871,38 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                 S.dropped_mass += probe.dropped_mass;
                 S.mass = probe.mass;
                 S.updates += probe.updates;
-                done += 2;
-                entry.ms[c] = probe.device_ms;
-                if (probe.device_ms < best) {
-                    best = probe.device_ms;
-                    entry.form = cand_form[c];
-                    entry.ty = cand_ty[c];
+                done += 1;
+                form = cand_form[c];
+                a.tile[1] = cand_ty[c];
+                if (!pr.warmed) {
+                    pr.warmed = true;
+                    continue;
                 }
+                pr.entry.ms[c] = probe.device_ms;
+                if (probe.device_ms < pr.best) {
+                    pr.best = probe.device_ms;
+                    pr.entry.form = cand_form[c];
+                    pr.entry.ty = cand_ty[c];
+                }
+                pr.cand++;
+                pr.warmed = false;
             }
-            if (st == VL_OK && complete) {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
+            entry = pr.entry;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (st == VL_OK && pr.cand >= 3) {
                 tune_store_locked(key, entry);
+                g_tune_progress.erase(key);
+                form = entry.form;
+                a.tile[1] = entry.ty;
+            } else {
+                g_tune_progress[key] = pr;
             }
+        } else {
+            form = entry.form;
+            a.tile[1] = entry.ty;
         }
         for (int c = 0; c < 3; c++) S.tune_ms[c] = entry.ms[c];
-        form = entry.form;
-        a.tile[1] = entry.ty;
+        if (form == VL_FORM_AUTO) form = entry.form;  // no step ran in this call
     }
     const bool fused = form != VL_FORM_3PASS;
     if (st == VL_OK && done < nsteps)

@@ -82,3 +82,27 @@ def test_tuning_cache_persists(tmp_path):
     assert second.returncode == 0, second.stderr
     assert len(cache.read_text().splitlines()) == 1  # reused, not re-tuned
     assert second.stdout.split() == first.stdout.split()
+
+
+def test_probing_advances_over_single_step_calls():
+    """Calls of one step each still tune: every call runs the next probe step, and once
+    the three candidates are timed the fastest form is used; f equals a fixed-form run.
+    (Every cell holds every block id, so the workload key stays the same across calls.)"""
+    n = (40, 33, 18)
+    init = inputs.random_blocks(n, (8, 8, 8), 1.0, seed=71)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0, -3.0, -4.5), dv=(1.0,) * 3)
+    ref, _ = run(mesh, init, 8, vlasov.VL_FORM_FUSED)
+    g = gpu_grid(mesh, 0.1)
+    g.set_blocks(init.off, init.ids, init.vals)
+    forms = []
+    for _ in range(8):
+        g.translate(0.2, "xyz", 1, vlasov.VL_FORM_AUTO, check=True)
+        s = g.stats()
+        forms.append(s.form_used)
+    assert forms[:6] == [vlasov.VL_FORM_FUSED] * 4 + [vlasov.VL_FORM_3PASS] * 2  # the probes
+    assert all(t > 0 for t in s.tune_ms)
+    best = int(np.argmin(list(s.tune_ms)))
+    assert forms[6] == forms[7] == (vlasov.VL_FORM_3PASS if best == 2 else vlasov.VL_FORM_FUSED)
+    for x, y in zip(ref, g.get_blocks()):
+        np.testing.assert_array_equal(x, y)
+    g.close()
