@@ -137,20 +137,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
-// Number of consecutive cells from x on (at most maxlen) set in both row bitmaps k and u.
-__device__ __forceinline__ int run_of_ones(const uint64_t* k, const uint64_t* u, int x, int maxlen)
-{
-    int n = 0;
-    while (n < maxlen) {
-        const int xx = x + n;
-        const uint64_t w = (k[xx >> 6] & u[xx >> 6]) >> (xx & 63);
-        const int avail = 64 - (xx & 63);
-        const int ones = (~w == 0ull) ? 64 : __ffsll((long long)~w) - 1;
-        n += min(ones, avail);
-        if (ones < avail) break;
-    }
-    return min(n, maxlen);
-}
 // 1D bulk copy global -> shared (TMA), completion counted on an mbarrier
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
 {
@@ -326,47 +312,52 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                                      (unsigned)(s_run[k][2] * NV * sizeof(T)), bar);
                     }
                 } else if (sbulk) {
-                    // lane u1 stages halo row u1: one bulk copy per run of present cells
-                    // (consecutive slots), zeros for absent ones; every lane adds its bytes
-                    // to the barrier's expected count before one lane arrives
+                    // lane u1 stages halo row u1.  The row's bitmap words are read once
+                    // (a run spans at most two); each run of present cells, whose slots are
+                    // consecutive, is one bulk copy announced to the barrier just before it
+                    // is issued; absent cells are zeroed.  One lane arrives after the warp
+                    // has issued everything, so the phase cannot complete early.
                     uint64_t* bar = &s_bar[(gstep + s) % NST];
                     if (ltid < EY) {
                         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                         const int64_t row = (int64_t)pr1[ltid] + r2;
-                        const uint64_t* krow = P.in.kbits + (int64_t)b * G.RW + row * G.W;
-                        const uint64_t* urow = P.in.ubits + (int64_t)b * G.RW + row * G.W;
-                        const uint32_t* wrow = P.in.woff + (int64_t)b * G.RW + row * G.W;
+                        const int64_t wbase = (int64_t)b * G.RW + row * G.W;
                         T* dst = st + ltid * SROW;
-                        unsigned bytes = 0;
-                        for (int pass = 0; pass < 2; pass++) {
-                            for (int k = 0; k < s_nrun; k++) {
-                                const int u0 = s_run[k][0], x0 = s_run[k][1], len = s_run[k][2];
-                                int u = 0;
-                                while (u < len) {
-                                    const int x = x0 + u;
-                                    if (!(((krow[x >> 6] & urow[x >> 6]) >> (x & 63)) & 1ull)) {
-                                        if (pass == 1) {
-                                            float4* z = reinterpret_cast<float4*>(dst + (u0 + u) * NV);
-                                            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int k = 0; k < s_nrun; k++) {
+                            const int u0 = s_run[k][0], x0 = s_run[k][1], len = s_run[k][2];
+                            const int w0 = x0 >> 6, sh = x0 & 63;
+                            const bool two = sh + len > 64;  // the run reaches into word w0+1
+                            const uint64_t ua = P.in.ubits[wbase + w0];
+                            const uint64_t ub = two ? P.in.ubits[wbase + w0 + 1] : 0ull;
+                            const uint32_t oa = P.in.woff[wbase + w0];
+                            const uint32_t ob = two ? P.in.woff[wbase + w0 + 1] : 0u;
+                            const uint64_t lenmask = (1ull << len) - 1ull;  // len <= EX < 64
+                            // bit u: cell x0 + u holds the block (sh >= 43 whenever two)
+                            uint64_t pm = (P.in.kbits[wbase + w0] & ua) >> sh;
+                            if (two) pm |= (P.in.kbits[wbase + w0 + 1] & ub) << (64 - sh);
+                            pm &= lenmask;
+                            uint64_t absent = ~pm & lenmask;
+                            while (absent) {
+                                const int u = __ffsll((long long)absent) - 1;
+                                absent &= absent - 1ull;
+                                float4* z = reinterpret_cast<float4*>(dst + (u0 + u) * NV);
+                                const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                                            for (int k2 = 0; k2 < PC; k2++) z[k2] = zero;
-                                        }
-                                        u++;
-                                        continue;
-                                    }
-                                    const int rl = run_of_ones(krow, urow, x, len - u);
-                                    if (pass == 0) {
-                                        bytes += (unsigned)(rl * NV * sizeof(T));
-                                    } else {
-                                        const int64_t r = (int64_t)wrow[x >> 6] +
-                                                          __popcll(urow[x >> 6] & ((1ull << (x & 63)) - 1ull));
-                                        bulk_g2s(dst + (u0 + u) * NV, ipool + ibase + r * NV,
-                                                 (unsigned)(rl * NV * sizeof(T)), bar);
-                                    }
-                                    u += rl;
-                                }
+                                for (int k2 = 0; k2 < PC; k2++) z[k2] = zero;
                             }
-                            if (pass == 0) mbar_add_tx(bar, bytes);
+                            uint64_t m = pm;
+                            while (m) {
+                                const int u = __ffsll((long long)m) - 1;
+                                const int rl = __ffsll((long long)~(m >> u)) - 1;  // run length
+                                const int x = x0 + u;
+                                const bool lo = (x >> 6) == w0;
+                                const int64_t r = (int64_t)(lo ? oa : ob) +
+                                                  __popcll((lo ? ua : ub) & ((1ull << (x & 63)) - 1ull));
+                                const unsigned bytes = (unsigned)(rl * NV * sizeof(T));
+                                mbar_add_tx(bar, bytes);
+                                bulk_g2s(dst + (u0 + u) * NV, ipool + ibase + r * NV, bytes, bar);
+                                m &= ~(((1ull << rl) - 1ull) << u);
+                            }
                         }
                     }
                     __syncwarp();
@@ -406,6 +397,28 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         auto out_ranks = [&](int s) {  // sparse output slots of the plane completed at s
             const int zo = out_of(s);
             if (dense_out || s < FIRST || zo < 0 || zo >= n2) return;
+            int* orow = orank + (s & 1) * TX * TY;
+            if (a0 == 0) {
+                // one tile row per lane of the second loader warp: its TX cells lie in one
+                // bitmap word (t0 is a multiple of TX, which divides 64)
+                const int j = ltid - 32;
+                if (j >= 0 && j < TY) {
+                    int64_t wbase = -1;
+                    if (j < e1) {
+                        const int64_t row = (int64_t)rpart(a1, t1 + j, ny) + rpart(a2, zo, ny);
+                        wbase = (int64_t)b * G.RW + row * G.W + (t0 >> 6);
+                    }
+                    const uint64_t uw = wbase >= 0 ? P.out.ubits[wbase] : 0ull;
+                    const uint32_t ow = wbase >= 0 ? P.out.woff[wbase] : 0u;
+#pragma unroll
+                    for (int i = 0; i < TX; i++) {
+                        const int bit = (t0 + i) & 63;
+                        const bool has = i < e0 && ((uw >> bit) & 1ull);
+                        orow[j * TX + i] = has ? (int)(ow + __popcll(uw & ((1ull << bit) - 1ull))) : -1;
+                    }
+                }
+                return;
+            }
             for (int c = ltid; c < TX * TY; c += NLD) {
                 int j = c / TX, i = c - j * TX;
                 int r = -1;
@@ -414,7 +427,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     int64_t row = (int64_t)rpart(a0, t0 + i, ny) + rpart(a1, t1 + j, ny) + rpart(a2, zo, ny);
                     r = (int)cell_rank(P.out, G, b, x, row, false);
                 }
-                orank[(s & 1) * TX * TY + c] = r;
+                orow[c] = r;
             }
         };
         auto keep_flags = [&](int s) {  // per-chunk keep flags of the plane completed at s
