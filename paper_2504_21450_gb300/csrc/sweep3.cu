@@ -190,6 +190,195 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     }
 }
 
+
+// ---- vector form: four velocity cells per thread ------------------------------------
+// Same walk as k_pass, but a thread owns one vx row (4 cells) of a velocity chunk and
+// moves it with 16-byte loads and stores (8-byte in 16-bit storage): four independent
+// walks per thread, a quarter of the memory instructions.  A CTA holds 16 pencils, which
+// are neighbours along x for the y and z passes, so a warp touches 128 contiguous bytes
+// per chunk.  The four cells of a thread share the walking direction: always for the y
+// and z passes (they differ only in vx), and for the x pass when no block straddles
+// v_x = 0 (the host checks; otherwise it launches k_pass).
+constexpr int kPen4 = 16;
+constexpr int kThreads4 = kPen4 * 16;
+constexpr int kBatch4 = 8;
+
+template <int kCodec>
+__device__ __forceinline__ void load4(const typename Codec<kCodec>::T* p, float sc, float (&o)[4])
+{
+    if constexpr (kCodec == 0) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    } else {
+        const uint2 raw = *reinterpret_cast<const uint2*>(p);
+        const typename Codec<kCodec>::T* h = reinterpret_cast<const typename Codec<kCodec>::T*>(&raw);
+#pragma unroll
+        for (int i = 0; i < 4; i++) o[i] = Codec<kCodec>::dec(h[i], sc);
+    }
+}
+
+template <int kCodec>
+__device__ __forceinline__ void store4(typename Codec<kCodec>::T* p, const typename Codec<kCodec>::T (&c)[4])
+{
+    if constexpr (kCodec == 0) {
+        *reinterpret_cast<float4*>(p) = make_float4(c[0], c[1], c[2], c[3]);
+    } else {
+        uint2 raw;
+        typename Codec<kCodec>::T* h = reinterpret_cast<typename Codec<kCodec>::T*>(&raw);
+#pragma unroll
+        for (int i = 0; i < 4; i++) h[i] = c[i];
+        *reinterpret_cast<uint2*>(p) = raw;
+    }
+}
+
+template <bool kLim, int kCodec>
+__global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
+{
+    using C = Codec<kCodec>;
+    using T = typename C::T;
+    extern __shared__ int s_rank4[];  // [kPen4][nd] input ranks, then output ranks
+    __shared__ int s_any[kPen4];
+    const GridGeom& G = P.G;
+    if (aborted(G.abort)) return;
+    const int b = (int)(blockIdx.x / P.groups);
+    const int64_t grp = blockIdx.x % P.groups;
+    const int nd = G.n[P.dim];
+    const int64_t npen = G.N / nd;
+    if (P.out.cnt[b] == 0) return;
+    int* s_rin = s_rank4;
+    int* s_rout = s_rank4 + kPen4 * nd;
+
+    if (threadIdx.x < kPen4) s_any[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kPen4 * nd; t += blockDim.x) {
+        int k = t / nd, i = t - k * nd;
+        int64_t p = grp * kPen4 + k;
+        int ri = -1, ro = -1;
+        if (p < npen) {
+            int x;
+            int64_t row;
+            pencil_cell(G, P.dim, p, i, x, row);
+            ri = (int)cell_rank(P.in, G, b, x, row, P.check_keep_in != 0);
+            ro = (int)cell_rank(P.out, G, b, x, row, false);
+        }
+        s_rin[k * nd + i] = ri;
+        s_rout[k * nd + i] = ro;
+        if (ro >= 0) s_any[k] = 1;
+    }
+    __syncthreads();
+    const int k = threadIdx.x >> 4;        // pencil; a warp holds pencils k and k^1
+    const int q = (threadIdx.x >> 2) & 3;  // velocity chunk (vz within the block)
+    const int vy = threadIdx.x & 3;        // vx row of the chunk
+    if (!s_any[k] && !s_any[k ^ 1]) return;  // warp-uniform
+
+    const int bc[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
+    WalkConst kc[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int within = P.dim == 0 ? i : (P.dim == 1 ? vy : q);
+        const int iv = bc[P.dim] * 4 + within;
+        kc[i] = walk_const((P.vmin + (iv + 0.5) * P.dv) * P.cs);
+    }
+    const bool up = kc[0].up != 0;
+    const bool uni = __all_sync(0xffffffffu, up) || __all_sync(0xffffffffu, !up);
+
+    const T* src = static_cast<const T*>(P.in.pool) +
+                   ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + 4 * vy;
+    T* dst = static_cast<T*>(P.out.pool) + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + 4 * vy;
+    const float sc_in = kCodec ? P.in.scale[b] : 1.0f;
+    const float sc_out = kCodec ? P.out.scale[b] : 1.0f;
+    const float inv_out = 1.0f / sc_out;
+    const int* rin = s_rin + k * nd;
+    const int* rout = s_rout + k * nd;
+    auto cell_at = [&](int m) { return up ? m : nd - 1 - m; };
+    auto load = [&](int m, float (&o)[4]) {
+        const int r = rin[cell_at(m)];
+        if (r >= 0) {
+            load4<kCodec>(src + (int64_t)r * kChunk, sc_in, o);
+        } else {
+            o[0] = o[1] = o[2] = o[3] = 0.0f;
+        }
+    };
+    float t0[4], t1[4];  // originals of walking positions 0 and 1 (the wrapped tail)
+    load(0, t0);
+    load(1 % nd, t1);
+
+    Walk<kLim> s[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) s[i].reset();
+    float msum = 0.0f;
+    float vmx = 0.0f;
+    double mass = 0.0;
+    const float thr = P.thr;
+    auto push_emit = [&](int m, const float (&a)[4]) {
+        float res[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) res[i] = s[i].push(a[i], kc[i]);
+        if (m < 2) return;
+        const int c = cell_at(m - 2);
+        const int r = rout[c];
+        T code[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            code[i] = C::enc(res[i], inv_out);
+            if (kCodec) res[i] = C::dec(code[i], sc_out);
+        }
+        if (r >= 0) store4<kCodec>(dst + (int64_t)r * kChunk, code);
+        if (P.last) {
+            const bool keep = r >= 0 && (res[0] >= thr || res[1] >= thr || res[2] >= thr || res[3] >= thr);
+            uint8_t* kq = P.keepq + ((int64_t)P.out.base[b] + r) * 4 + q;
+            if (uni) {
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                const unsigned nib = (bal >> ((threadIdx.x & 31) & ~3u)) & 0xfu;  // the chunk's 4 rows
+                if (nib && vy == 0) *kq = 1;
+            } else if (keep) {
+                *kq = 1;
+            }
+            if (r >= 0) {
+                msum += (res[0] + res[1]) + (res[2] + res[3]);
+                if (kCodec) vmx = fmaxf(vmx, fmaxf(fmaxf(fabsf(res[0]), fabsf(res[1])), fmaxf(fabsf(res[2]), fabsf(res[3]))));
+            }
+        }
+    };
+    int m = -3;
+    for (; m < 0; m++) {
+        float a[4];
+        load(wrapi(m, nd), a);
+#pragma unroll
+        for (int i = 0; i < 4; i++) s[i].push(a[i], kc[i]);
+    }
+    for (; m + kBatch4 <= nd; m += kBatch4) {
+        float a[kBatch4][4];
+#pragma unroll
+        for (int u = 0; u < kBatch4; u++) load(m + u, a[u]);
+#pragma unroll
+        for (int u = 0; u < kBatch4; u++) push_emit(m + u, a[u]);
+        if (P.last) {
+            mass += (double)msum;
+            msum = 0.0f;
+        }
+    }
+    for (; m < nd; m++) {
+        float a[4];
+        load(m, a);
+        push_emit(m, a);
+    }
+    push_emit(m, t0);
+    push_emit(m + 1, t1);
+    if (P.last) {
+        mass += (double)msum;
+        for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
+        if ((threadIdx.x & 31) == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
+        if (kCodec) {
+            unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
+            if ((threadIdx.x & 31) == 0 && u) atomicMax(&P.out.vmax[b], u);
+        }
+    }
+}
+
 }  // namespace
 
 vl_status run_3pass(Grid* g, const StepArgs& a)
@@ -217,13 +406,30 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         P.keepq = B.keepq;
         P.ctr = a.ctr;
         int64_t npen = G.N / G.n[d];
-        P.groups = (npen + kPencils - 1) / kPencils;
+        // the vector kernel needs one walking direction per vx row: along x, no block
+        // may straddle v_x = 0
+        bool vec = true;
+        if (d == 0)
+            for (int bx = 0; bx < G.nbx && vec; bx++) {
+                const double lo = P.vmin + (4 * bx + 0.5) * P.dv, hi = P.vmin + (4 * bx + 3.5) * P.dv;
+                if ((lo >= 0.0) != (hi >= 0.0)) vec = false;
+            }
+        const int per_cta = vec ? kPen4 : kPencils;
+        P.groups = (npen + per_cta - 1) / per_cta;
         int64_t nblocks = P.groups * G.nb;
         if (nblocks > 0x7fffffffLL) return fail(g, VL_EINVAL, "3-pass form: grid too large");
+        const int smem4 = 2 * kPen4 * G.n[d] * (int)sizeof(int);
         with_codec(g->codec, [&](auto c) {
             constexpr int kc = decltype(c)::value;
-            if (a.limiter) k_pass<true, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
-            else k_pass<false, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
+            if (vec) {
+                auto kern = a.limiter ? k_pass4<true, kc> : k_pass4<false, kc>;
+                if (smem4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4);
+                kern<<<(unsigned)nblocks, kThreads4, smem4, g->stream>>>(P);
+            } else if (a.limiter) {
+                k_pass<true, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
+            } else {
+                k_pass<false, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
+            }
         });
         note_launch();
     }
