@@ -231,7 +231,10 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
     int done_total = 0;
     while (st == VL_OK && done_total < nsteps) {
         const int n = nsteps - done_total;
-        // buffers the captured steps use, sized before capture
+        // buffers the captured steps use, sized before capture.  When the state's pool
+        // must grow, the next layout's pool (which holds nothing yet) is released first,
+        // so that the growth never needs three pools at once.
+        if (g->lay[g->cur].capacity < cap) layout_release_pool(g, g->lay[1 - g->cur]);
         st = layout_grow_pool(g, g->lay[g->cur], cap);
         if (st == VL_OK) st = layout_ensure_pool(g, g->lay[1 - g->cur], cap);
         if (st == VL_OK && fused) st = fused_worklist_alloc(g, a);

@@ -96,6 +96,8 @@ vl_status cuda_fail(Grid* g, cudaError_t e, const char* what);
 vl_status layout_alloc_meta(Grid* g, Layout& L);
 void layout_free(Grid* g, Layout& L);
 vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks);
+// Frees a layout's value pool and keep flags (its bitmaps stay).
+void layout_release_pool(Grid* g, Layout& L);
 // 16-bit storage: scale of the next layout's codes from the current layout's largest
 // values (translation with the limiter creates no new maximum), and its vmax cleared.
 void launch_out_scale(Grid* g, const Layout& cur, Layout& next);

@@ -584,6 +584,16 @@ void layout_free(Grid* g, Layout& L)
     L = Layout{};
 }
 
+void layout_release_pool(Grid* g, Layout& L)
+{
+    cudaStreamSynchronize(g->stream);  // no queued kernel may still use the pool
+    g->release(L.pool);
+    g->release(L.keepq);
+    L.pool = nullptr;
+    L.keepq = nullptr;
+    L.capacity = 0;
+}
+
 vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks)
 {
     if (blocks <= L.capacity && L.pool) return VL_OK;
