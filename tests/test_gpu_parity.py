@@ -277,3 +277,30 @@ def test_sparse_config_window_in_captured_steps(name, n, origin):
     # the two forms agree bit for bit (z-last order)
     for a, b in zip(*posts):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("vmin", [(-3.0, -4.0, -4.5), (-3.0, -2.0, -1.0)])
+def test_blocks_straddling_zero_velocity(vmin):
+    """Velocity blocks whose cells move both ways along a sweep axis: along x the 3-pass
+    form falls back to its one-cell-per-thread kernel (a thread of the vector kernel walks
+    four vx cells in one direction); along y and z the threads of a warp walk in
+    different directions.  Both forms against the oracle, step by step, and the fused
+    form against the 3-pass form (z-last order: bit for bit)."""
+    n = (21, 14, 9)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.5, seed=48)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=vmin, dv=(1.0,) * 3)
+    outs = []
+    for form in ("fused", "3pass"):
+        g = gpu_grid(mesh, 0.2)
+        g.set_blocks(init.off, init.ids, init.vals)
+        before = as_ref(init)
+        for step in range(2):
+            g.translate(0.15, "xyz", 1, FORMS[form], check=True)
+            after = g.get_blocks()
+            err, fmax, amb, ref, st = compare_step(mesh, before, after, 0.2, 0.15, "xyz")
+            assert err <= VAL_TOL * fmax, (form, step, err, fmax)
+            before = oracle.as_blocks(*[np.asarray(a) for a in after[:2]], after[2].astype(np.float64))
+        outs.append(g.get_blocks())
+        g.close()
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
