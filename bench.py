@@ -156,6 +156,13 @@ def cpu_baseline(cfg, budget_s=20.0):
                       f"cells ({blk.nblocks * 64:.3g} updates/step), FP64, OpenMP over block ids"}
 
 
+def workload_name(cfg) -> str:
+    """The workload both arms report in config.workload."""
+    return (f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} periodic cells x "
+            f"{cfg.nv[0]}x{cfg.nv[1]}x{cfg.nv[2]} velocity cells (4^3 blocks), "
+            f"dt={cfg.dt}, rel. threshold {cfg.rel_threshold:g}")
+
+
 def run_reference(args, cfg):
     """Reference arm: the FP64 oracle timed on the host cores, bounded window per step."""
     import oracle
@@ -185,9 +192,9 @@ def run_reference(args, cfg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} cells x "
-                               f"{cfg.nv[0]}^3 velocity cells, periodic {edge}^3-cell window per step",
-                   "sample_cells": edge ** 3, "order": "xyz"},
+        "config": {"workload": workload_name(cfg), "order": "xyz",
+                   "sample": f"each step: a periodic {edge}^3-cell window of the workload "
+                             f"({edge ** 3} cells, the full velocity mesh)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"periodic {edge}^3-cell window of the workload per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -436,9 +443,7 @@ def run_ours(args, cfg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} periodic cells x "
-                               f"{cfg.nv[0]}x{cfg.nv[1]}x{cfg.nv[2]} velocity cells (4^3 blocks), "
-                               f"dt={cfg.dt}, rel. threshold {cfg.rel_threshold:g}",
+        "config": {"workload": workload_name(cfg),
                    "form": form_used, "storage": args.storage, "order": args.order, "parallelism": f"replicas{world}",
                    "graph": bool(args.graph), "capacity_regrows": regrows,
                    "l2": f"state ({updates / args.steps * STORAGE_BYTES[args.storage] / 1e9:.1f} GB per copy) larger than L2; no flush",
