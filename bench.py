@@ -156,6 +156,17 @@ def cpu_baseline(cfg, budget_s=20.0):
                       f"cells ({blk.nblocks * 64:.3g} updates/step), FP64, OpenMP over block ids"}
 
 
+def aggregate(el_ms: float, updates: float, dist=None, device="cuda"):
+    """Whole-job figures of the ranks: the slowest rank's time and the sum of the updates
+    (each rank advances its own replica of the workload)."""
+    import torch
+    t = torch.tensor([el_ms, float(updates)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1])
+
+
 def workload_name(cfg) -> str:
     """The workload both arms report in config.workload."""
     return (f"{cfg.name}: {cfg.n[0]}x{cfg.n[1]}x{cfg.n[2]} periodic cells x "
@@ -386,14 +397,7 @@ def run_ours(args, cfg):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    el_ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([el_ms, float(updates)], dtype=torch.float64, device="cuda")
-    if dist:
-        tm = t.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        t = tm
-    el_ms, total_updates = float(t[0]), float(t[1])
+    el_ms, total_updates = aggregate(ev0.elapsed_time(ev1), updates, dist, "cuda")
     value = total_updates / (el_ms / 1e3)
 
     # end to end through the public API with host buffers: H2D of the state, one step,
