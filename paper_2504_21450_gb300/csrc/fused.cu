@@ -54,7 +54,7 @@ struct Shape {
     static constexpr int STAGE = EY * SROW;
     static constexpr int XBUF = EY * XROW;
     static constexpr int TABS = 2 * EX + 2 * EY;
-    static constexpr int SMEM = NST * STAGE * ES + XBUF * 4 + TABS * 4 + 2 * TX * TY * 4 + 2 * 16 * 4 + 64;
+    static constexpr int SMEM = NST * STAGE * ES + 2 * XBUF * 4 + TABS * 4 + 4 * TX * TY * 4 + 3 * 16 * 4 + 64;
     static_assert(NX < NT, "sweep-0 rows must leave threads to stage planes");
     static_assert(NH * TX * NV == NT && NH * L == TY, "sweep-1 segments must tile the CTA");
 };
@@ -165,12 +165,12 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
     extern __shared__ __align__(16) float smem[];
     T* stage = reinterpret_cast<T*>(smem);
     float* xbuf = reinterpret_cast<float*>(stage + NST * S::STAGE);
-    int* px0 = reinterpret_cast<int*>(xbuf + S::XBUF);
+    int* px0 = reinterpret_cast<int*>(xbuf + 2 * S::XBUF);  // xbuf: [2] planes
     int* pr0 = px0 + EX;
     int* px1 = pr0 + EX;
     int* pr1 = px1 + EY;
-    int* orank = pr1 + EY;                                           // [2][TY][TX]
-    unsigned* kb = reinterpret_cast<unsigned*>(orank + 2 * TX * TY);  // [2][16 warps]
+    int* orank = pr1 + EY;                                           // [4][TY][TX]
+    unsigned* kb = reinterpret_cast<unsigned*>(orank + 4 * TX * TY);  // [3][16 warps]
     __shared__ int64_t s_work;
     __shared__ __align__(8) uint64_t s_bar[NST];  // staging barriers of the bulk copies
     __shared__ int s_run[EX][3];                  // contiguous runs of a halo row: u0, x, len
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         auto out_ranks = [&](int s) {  // sparse output slots of the plane completed at s
             const int zo = out_of(s);
             if (dense_out || s < FIRST || zo < 0 || zo >= n2) return;
-            int* orow = orank + (s & 1) * TX * TY;
+            int* orow = orank + (s & 3) * TX * TY;
             if (a0 == 0) {
                 // one tile row per lane of the second loader warp: its TX cells lie in one
                 // bitmap word (t0 is a multiple of TX, which divides 64)
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         auto keep_flags = [&](int s) {  // per-chunk keep flags of the plane completed at s
             const int zo = out_of(s);
             if (s < FIRST || zo < 0 || zo >= n2) return;
-            const unsigned* km = kb + (s & 1) * 16;
+            const unsigned* km = kb + (s % 3) * 16;
             for (int c = ltid; c < TX * TY; c += NLD) {
                 int j = c / TX, i = c - j * TX;
                 if (i >= e0 || j >= e1) continue;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     int64_t row = (int64_t)rpart(a0, t0 + i, ny) + rpart(a1, t1 + j, ny) + rpart(a2, zo, ny);
                     r = row * G.n[0] + x;
                 } else {
-                    r = orank[(s & 1) * TX * TY + c];
+                    r = orank[(s & 3) * TX * TY + c];
                 }
                 if (r < 0) continue;
                 int hh = j / L, jj = j - hh * L;
@@ -470,11 +470,17 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         auto step = [&](int s, auto emit_tag) {
             constexpr bool kEmit = decltype(emit_tag)::value;
             wait_plane(s);
-            __syncthreads();  // plane s staged; previous readers of xbuf done
+            // Bulk-staged planes: each thread's barrier wait makes plane s visible to it,
+            // and every buffer written in this half of the step is one that no thread
+            // can still be reading from the previous step: xbuf is double-buffered, the
+            // output ranks have four slots, the keep-flag words three, the flags are
+            // taken two planes late, and the stage refilled now was last read before the
+            // previous step's second barrier.  cp.async-staged planes need the barrier.
+            if (!(bulk || sbulk)) __syncthreads();
             if (!loader) {
                 // sweep 0 along axis 0 on halo row `hi`
                 const T* line = stage + (s % NST) * S::STAGE + hi * SROW + v;
-                float* xo = xbuf + hi * XROW + v;
+                float* xo = xbuf + (s & 1) * S::XBUF + hi * XROW + v;
                 Walk<kLim> wk;
                 wk.reset();
                 if (kw[0].up) {
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     }
                 }
             } else {
-                keep_flags(s - 1);
+                keep_flags(s - 2);
                 out_ranks(s + 1);
                 issue_plane(s + NST - 1);
             }
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                           (int64_t)zo * P.stride[a2]) * NV;
             const int64_t dstep = P.stride[a1] * NV;
             const bool fast = dense_out && full;
-            const int* orow = orank + (s & 1) * TX * TY + j0 * TX + ci;
+            const int* orow = orank + (s & 3) * TX * TY + j0 * TX + ci;
             float psum = 0.0f;
             unsigned kmask = 0;
             auto consume = [&](int jj, float yv) {
@@ -536,7 +542,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     if (res >= P.thr) kmask |= 1u << jj;
                 }
             };
-            const float* line = xbuf + (j0 * XROW) + ci * NV + v;
+            const float* line = xbuf + (s & 1) * S::XBUF + (j0 * XROW) + ci * NV + v;
             Walk<kLim> wk;
             wk.reset();
             if (kw[1].up) {
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             }
             if (kEmit) {
                 unsigned km = __reduce_or_sync(0xffffffffu, kmask << (16 * (ci & 1)));
-                if (lane == 0) kb[(s & 1) * 16 + warp] = km;
+                if (lane == 0) kb[(s % 3) * 16 + warp] = km;
                 float y = psum - mcomp;
                 float t = msum + y;
                 mcomp = (t - msum) - y;
@@ -566,7 +572,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         for (; s < nsteps; s++) step(s, std::true_type{});
 
         __syncthreads();
-        if (loader) keep_flags(nsteps - 1);
+        if (loader) {
+            keep_flags(nsteps - 2);
+            keep_flags(nsteps - 1);
+        }
         cp_async_wait<0>();
         if (bulk || sbulk) gstep += (unsigned)nsteps;
         double m = (double)msum;
