@@ -135,12 +135,13 @@ def test_auto_form_with_16bit_storage_tunes_tiles_only():
 
 def test_precision_workload_error_report():
     """The 32x32x8 periodic grid with the uniform workload's distributions (32^3
-    velocity cells, 5% density noise): 10 steps in FP32, bfloat16 and float16 storage
-    against the FP64 oracle from the same float32 input.  FP32 meets the acceptance
-    tolerance; the 16-bit errors are reported (max-abs and L1, relative to max f, and
-    the mass change) and gated only at a few units of their rounding."""
+    velocity cells, 5% density noise): 10 steps (VLGT_PRECISION_STEPS to change) in FP32,
+    bfloat16 and float16 storage against the FP64 oracle from the same float32 input.
+    FP32 meets the acceptance tolerance; the 16-bit errors are reported (max-abs, L1 and
+    L2 relative to the oracle's max, L1 and L2 norms, and the mass change) and gated only
+    at a few units of their rounding."""
     cfg = inputs.CONFIGS["precision"]
-    nsteps = 10
+    nsteps = int(os.environ.get("VLGT_PRECISION_STEPS", "10"))
     init = inputs.generate(cfg)
     off, ids, vals, thr = init.off, init.ids, init.vals, init.threshold
     mesh = oracle.Mesh(n=cfg.n, nv=cfg.nv, vmin=cfg.vmin, dv=cfg.dv, dx=cfg.dx)
@@ -167,6 +168,7 @@ def test_precision_workload_error_report():
                 d = np.abs(v2.astype(np.float64) - ref.vals)
                 entry["max_abs_rel"] = float(d.max()) / fmax
                 entry["l1_rel"] = float(d.sum() / np.abs(ref.vals).sum())
+                entry["l2_rel"] = float(np.sqrt((d * d).sum() / (ref.vals * ref.vals).sum()))
             report[f"{name}_{fname}"] = entry
     print(json.dumps(report))
     path = os.environ.get("VLGT_PRECISION_REPORT")
