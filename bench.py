@@ -423,7 +423,9 @@ def run_ours(args, cfg):
             te = torch.tensor([e_el], dtype=torch.float64, device="cuda")
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
             e_el = float(te[0])
-        h2d = h_off.numel() * 8 + h_ids.numel() * 2 + h_vals.numel() * 4
+        # 16-bit storage reads the host values twice: once for the per-id scales, once
+        # to store the codes
+        h2d = h_off.numel() * 8 + h_ids.numel() * 2 + h_vals.numel() * 4 * (1 if args.storage == "f32" else 2)
         e2e = {"value": e_updates * world / e_el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": 56 + 8, "steps": e_steps}
     elif e2e_note:

@@ -561,6 +561,7 @@ vl_status vl_grid_destroy(vl_grid* grid)
     g->release(g->item_mass);
     if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     g->release(g->abort_flag);
     g->release(g->step_ctr);
     if (g->step_ctr_host) cudaFreeHost(g->step_ctr_host);

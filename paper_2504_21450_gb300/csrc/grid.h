@@ -70,6 +70,7 @@ struct Grid {
     uint64_t graph_key = 0;
     int64_t graph_kernels = 0;            // kernels in the cached graph
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;   // host-to-device staging of vl_set_blocks
     float4* ctab = nullptr;               // device [2][3][nvmax] sweep constants
     float4* ctab_host = nullptr;          // pinned staging of the same
     double ctab_dt = -1.0;                // dt the table was built for

@@ -762,18 +762,45 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
         note_launch();
     }
     const int64_t chunk = std::min<int64_t>(std::max<int64_t>(M, 1), (int64_t)1 << 22);  // 1 GiB of values
-    float* stage_buf = nullptr;
-    if (M > 0 && !on_device) {
-        // host values: copied in chunks, so the device never holds a second full copy
-        stage_buf = (float*)sc.get((size_t)chunk * 256);
-        if (!stage_buf) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
+    // host values: copied in chunks (the device never holds a second full copy) through
+    // two staging buffers on a copy stream, so that the copy of one chunk overlaps the
+    // kernel that consumes the previous one
+    float* stage_buf[2] = {nullptr, nullptr};
+    cudaEvent_t ready = nullptr, copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    const bool staged = M > 0 && !on_device;
+    const int npass = (g->codec && !given) ? 2 : 1;
+    // two buffers when more than one chunk goes through them (over both passes)
+    const int nbuf = (npass * ((M + chunk - 1) / chunk) > 1) ? 2 : 1;
+    if (staged) {
+        for (int i = 0; i < nbuf; i++) {
+            stage_buf[i] = (float*)sc.get((size_t)chunk * 256);
+            if (!stage_buf[i]) return fail(g, VL_ENOMEM, "vl_set_blocks: staging allocation failed");
+        }
+        if (!g->copy_stream) {
+            e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks: copy stream");
+        }
+        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        for (int i = 0; i < 2; i++) {
+            cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming);
+        }
+        cudaEventRecord(ready, s);  // the staging buffers are free for the copy stream
+        cudaStreamWaitEvent(g->copy_stream, ready, 0);
     }
+    int64_t k = 0;  // chunk counter over both passes (staging buffer k % nbuf)
     for (int pass = (g->codec && !given ? 0 : 1); pass < 2 && M > 0; pass++) {
-        for (int64_t t0 = 0; t0 < M; t0 += (on_device ? M : chunk)) {
+        for (int64_t t0 = 0; t0 < M; t0 += (on_device ? M : chunk), k++) {
             const int64_t m = on_device ? M : std::min(chunk, M - t0);
-            const float* v = on_device ? vals : stage_buf;
-            if (!on_device)
-                cudaMemcpyAsync(stage_buf, vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice, s);
+            const int bi = (int)(k % nbuf);
+            const float* v = on_device ? vals : stage_buf[bi];
+            if (staged) {
+                if (k >= nbuf) cudaStreamWaitEvent(g->copy_stream, used[bi], 0);  // chunk k-nbuf consumed
+                cudaMemcpyAsync(stage_buf[bi], vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice,
+                                g->copy_stream);
+                cudaEventRecord(copied[bi], g->copy_stream);
+                cudaStreamWaitEvent(s, copied[bi], 0);
+            }
             if (pass == 0) {
                 k_block_vmax<<<nblk(m * 32, 256), 256, 0, s>>>(ids, v, t0, m, L.vmax);
             } else {
@@ -782,10 +809,19 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
                 });
             }
             note_launch();
+            if (staged) cudaEventRecord(used[bi], s);
         }
         if (pass == 0) {
             k_scale_from_vmax<<<nblk(G.nb, 256), 256, 0, s>>>(L.vmax, L.scale, G.nb);
             note_launch();
+        }
+    }
+    if (staged) {
+        cudaStreamSynchronize(s);  // every copy was waited for by a kernel on s
+        cudaEventDestroy(ready);
+        for (int i = 0; i < 2; i++) {
+            cudaEventDestroy(copied[i]);
+            cudaEventDestroy(used[i]);
         }
     }
     e = cudaStreamSynchronize(s);
