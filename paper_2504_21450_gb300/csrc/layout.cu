@@ -477,7 +477,12 @@ __global__ void k_block_vmax(const uint16_t* __restrict__ ids, const float* __re
     if (t >= m) return;
     float a = fmaxf(fabsf(vals[t * 64 + lane]), fabsf(vals[t * 64 + 32 + lane]));
     unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(a));
-    if (lane == 0 && u) atomicMax(&vmax[ids[t0 + t]], u);
+    // a plain read first: most blocks do not raise their id's maximum, and a stale read
+    // only costs an atomic that changes nothing
+    if (lane == 0 && u) {
+        unsigned* dst = &vmax[ids[t0 + t]];
+        if (u > *(volatile unsigned*)dst) atomicMax(dst, u);
+    }
 }
 
 // scale[b] = smallest power of two >= max |f| of block id b
