@@ -127,24 +127,32 @@ vl_status enqueue_step(Grid* g, StepArgs a, bool fused, bool graph, int64_t capa
     Layout& A = g->lay[g->cur];
     Layout& B = g->lay[1 - g->cur];
     a.ctr = ctr;
-    cudaMemsetAsync(ctr, 0, sizeof(StepCounters), g->stream);
-    launch_union(g, A, B);
-    launch_out_scale(g, A, B);
-    if (graph) {
-        launch_index(g, B);
-        launch_capacity_check(g, B, capacity, ctr);
-        cudaMemsetAsync(B.keepq, 0, (size_t)capacity * 4, g->stream);
-    } else {
-        int64_t total = 0;
-        vl_status st = layout_index(g, B, &total);
-        if (st != VL_OK) return st;
-        st = layout_ensure_pool(g, B, std::max<int64_t>(total, 1));
-        if (st != VL_OK) return st;
-        cudaMemcpyAsync(&ctr->needed, B.base + g->geom.nb, 8, cudaMemcpyDeviceToDevice, g->stream);
-        cudaMemsetAsync(B.keepq, 0, (size_t)std::max<int64_t>(total, 1) * 4, g->stream);
+    NvtxRange step_range("vl step");
+    {
+        NvtxRange range("union + index");
+        cudaMemsetAsync(ctr, 0, sizeof(StepCounters), g->stream);
+        launch_union(g, A, B);
+        launch_out_scale(g, A, B);
+        if (graph) {
+            launch_index(g, B);
+            launch_capacity_check(g, B, capacity, ctr);
+            cudaMemsetAsync(B.keepq, 0, (size_t)capacity * 4, g->stream);
+        } else {
+            int64_t total = 0;
+            vl_status st = layout_index(g, B, &total);
+            if (st != VL_OK) return st;
+            st = layout_ensure_pool(g, B, std::max<int64_t>(total, 1));
+            if (st != VL_OK) return st;
+            cudaMemcpyAsync(&ctr->needed, B.base + g->geom.nb, 8, cudaMemcpyDeviceToDevice, g->stream);
+            cudaMemsetAsync(B.keepq, 0, (size_t)std::max<int64_t>(total, 1) * 4, g->stream);
+        }
     }
-    vl_status st = fused ? run_fused(g, a) : run_3pass(g, a);
-    if (st != VL_OK) return st;
+    {
+        NvtxRange range(fused ? "sweeps (fused)" : "sweeps (3-pass)");
+        vl_status st = fused ? run_fused(g, a) : run_3pass(g, a);
+        if (st != VL_OK) return st;
+    }
+    NvtxRange range("sparsity rule");
     launch_pack_keep(g, B, ctr);
     return VL_OK;
 }
@@ -769,6 +777,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
 {
     if (!grid) return VL_EINVAL;
     Grid* g = reinterpret_cast<Grid*>(grid);
+    NvtxRange range("vl_translate");
     DeviceGuard dg(g->dev.device);
     vl_translate_opts opts;
     if (opts_in) opts = *opts_in;

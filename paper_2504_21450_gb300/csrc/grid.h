@@ -2,6 +2,7 @@
 // translation units of libvlgt (internal; the public interface is include/vlasov.h).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <type_traits>
 #include <vector>
@@ -154,6 +155,15 @@ struct StepArgs {
 // that are not complete at their first poll as overdue (VL_ETIMEOUT) -- they still
 // complete, so no copy is left in flight.
 bool fault_requested(const char* what);
+
+// NVTX range over a host scope (phases of a step show up in a timeline profiler; the
+// calls cost next to nothing when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Calls f(std::integral_constant<int, k>{}) for storage codec k (0 float32, 1 bfloat16,
 // 2 float16), so that one launch site instantiates the kernel for every codec.
