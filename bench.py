@@ -375,7 +375,7 @@ def run_ours(args, cfg):
     launches = 0
     regrows = 0
     replays = 0
-    phases = {"index_ms": 0.0, "sweep_ms": 0.0, "prune_ms": 0.0}
+    phases = {"index_ms": 0.0, "sweep_ms": 0.0, "prune_ms": 0.0, "tail_ms": 0.0}
     stats = None
     with ClockSampler(local) as clk:
         ev0.record(stream)

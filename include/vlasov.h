@@ -149,6 +149,10 @@ typedef struct {
                                8-row tile, 3-pass; 0 = not probed in this call */
     int64_t updates;        /* phase-space cell updates of the call: velocity cells present
                                at the start of each step, summed over its steps */
+    double tail_ms;         /* fused steps run one by one: summed over steps, the time from
+                               the first to the last CTA of the persistent sweep kernel
+                               running out of work (the single-GPU counterpart of the
+                               paper's wait time, Table 1); 0 otherwise */
 } vl_step_stats;
 
 void vl_translate_opts_default(vl_translate_opts* opts);

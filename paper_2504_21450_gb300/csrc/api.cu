@@ -169,6 +169,15 @@ vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_s
 {
     a.ev0 = g->ev_sweep0;
     a.ev1 = g->ev_sweep1;
+    // finish times of the fused kernel's CTAs (its idle tail, reported as tail_ms)
+    if (fused && !g->cta_done) {
+        g->cta_done = (uint64_t*)g->alloc((size_t)kMaxCtas * 8);
+        if (g->cta_done && cudaMallocHost((void**)&g->cta_done_host, (size_t)kMaxCtas * 8) != cudaSuccess) {
+            cudaGetLastError();
+            g->cta_done_host = nullptr;
+        }
+    }
+    a.stamp_ctas = fused && g->cta_done && g->cta_done_host;
     cudaEvent_t e0, e1, ep;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -181,6 +190,9 @@ vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_s
         cudaEventRecord(e1, g->stream);
         cudaMemcpyAsync(g->counters_host, g->counters, sizeof(StepCounters), cudaMemcpyDeviceToHost,
                         g->stream);
+        const int nct = a.stamp_ctas ? g->cta_count : 0;
+        if (nct > 0)
+            cudaMemcpyAsync(g->cta_done_host, g->cta_done, (size_t)nct * 8, cudaMemcpyDeviceToHost, g->stream);
         cudaError_t e = cudaStreamSynchronize(g->stream);
         if (e != cudaSuccess) {
             st = cuda_fail(g, e, "vl_translate step");
@@ -195,6 +207,14 @@ vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_s
         S->index_ms += ms;
         cudaEventElapsedTime(&ms, g->ev_sweep1, e1);
         S->prune_ms += ms;
+        if (nct > 0) {
+            uint64_t lo = ~0ull, hi = 0;
+            for (int c = 0; c < nct; c++) {
+                lo = std::min(lo, g->cta_done_host[c]);
+                hi = std::max(hi, g->cta_done_host[c]);
+            }
+            S->tail_ms += (double)(hi - lo) * 1e-6;
+        }
         const StepCounters& C = *g->counters_host;
         if (C.error) {
             st = step_error(g, C);
@@ -576,6 +596,8 @@ vl_status vl_grid_destroy(vl_grid* grid)
     if (g->ev_sweep0) cudaEventDestroy(g->ev_sweep0);
     if (g->ev_sweep1) cudaEventDestroy(g->ev_sweep1);
     for (cudaEvent_t ev : g->graph_ev) cudaEventDestroy(ev);
+    g->release(g->cta_done);
+    if (g->cta_done_host) cudaFreeHost(g->cta_done_host);
     g->release(g->ctab);
     if (g->ctab_host) cudaFreeHost(g->ctab_host);
     if (g->counters_host) cudaFreeHost(g->counters_host);
@@ -878,6 +900,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                 S.sweep_ms += probe.sweep_ms;
                 S.index_ms += probe.index_ms;
                 S.prune_ms += probe.prune_ms;
+                S.tail_ms += probe.tail_ms;
                 S.blocks = probe.blocks;
                 S.union_blocks = probe.union_blocks;
                 S.dropped_blocks = probe.dropped_blocks;

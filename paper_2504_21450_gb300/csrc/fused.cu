@@ -75,6 +75,7 @@ struct FusedArgs {
     StepCounters* ctr;
     int report_late;     // testing hook: a staging wait that is not complete at its first
                          // poll is reported as overdue (VL_ETIMEOUT), then waited for
+    uint64_t* cta_done;  // optional [gridDim.x]: %globaltimer when the CTA ran out of work
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
@@ -586,6 +587,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             if (lane == 0 && u) atomicMax(&P.out.vmax[b], u);
         }
     }
+    if (P.cta_done && tid == 0) P.cta_done[blockIdx.x] = globaltimer_ns();
 }
 
 // ---- work list ------------------------------------------------------------------
@@ -658,7 +660,11 @@ vl_status launch_fused(Grid* g, const FusedArgs& P)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     if (per_sm < 1) per_sm = 1;
-    kern<<<nsm * per_sm, NT, smem, g->stream>>>(P);
+    FusedArgs Q = P;
+    const int nct = nsm * per_sm;
+    if (nct > kMaxCtas) Q.cta_done = nullptr;
+    g->cta_count = Q.cta_done ? nct : 0;
+    kern<<<nct, NT, smem, g->stream>>>(Q);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(g, e, "fused sweep launch");
@@ -742,6 +748,7 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.keepq = B.keepq;
     P.ctr = a.ctr;
     P.report_late = fault_requested("timeout") ? 1 : 0;
+    P.cta_done = a.stamp_ctas ? g->cta_done : nullptr;
     record_sweep_event(a.ev0, g->stream, a.ev_node);
     vl_status st = VL_OK;
     with_codec(g->codec, [&](auto c) {
@@ -784,6 +791,7 @@ vl_status launch_fused_dense(const GridGeom& G, const LayoutView& in, const Layo
     P.keepq = nullptr;
     P.ctr = ctr;
     P.report_late = 0;
+    P.cta_done = nullptr;
     Grid tmp;  // launch helper needs the device and the stream only
     tmp.dev.device = device;
     tmp.stream = stream;

@@ -72,6 +72,9 @@ struct Grid {
     int64_t graph_kernels = 0;            // kernels in the cached graph
     cudaStream_t capture_stream = nullptr;
     cudaStream_t copy_stream = nullptr;   // host-to-device staging of vl_set_blocks
+    uint64_t* cta_done = nullptr;         // device [kMaxCtas]: finish time of each fused CTA
+    uint64_t* cta_done_host = nullptr;    // pinned copy
+    int cta_count = 0;                    // CTAs of the last fused launch
     float4* ctab = nullptr;               // device [2][3][nvmax] sweep constants
     float4* ctab_host = nullptr;          // pinned staging of the same
     double ctab_dt = -1.0;                // dt the table was built for
@@ -148,6 +151,7 @@ struct StepArgs {
     int nvmax;
     StepCounters* ctr;    // counters of this step
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the sweep kernels when set
+    bool stamp_ctas = false;  // fused kernel: each CTA records when it ran out of work
     bool ev_node = false;  // inside a stream capture: record as event record nodes
 };
 // Host-side fault injection for tests: true when the environment variable VLGT_FAULT
@@ -183,6 +187,7 @@ inline void record_sweep_event(cudaEvent_t ev, cudaStream_t s, bool node)
     if (node) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
     else cudaEventRecord(ev, s);
 }
+constexpr int kMaxCtas = 4096;  // CTAs of a persistent fused launch, at most
 vl_status fused_worklist_alloc(Grid* g, const StepArgs& a);
 int tile_rows(const StepArgs& a);
 vl_status run_fused(Grid* g, const StepArgs& a);

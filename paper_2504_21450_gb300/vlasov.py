@@ -55,7 +55,7 @@ class vl_step_stats(ctypes.Structure):
                 ("graph_replays", ctypes.c_int64), ("capacity_regrows", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("form_used", ctypes.c_int),
                 ("tile_rows_used", ctypes.c_int), ("tune_ms", ctypes.c_double * 3),
-                ("updates", ctypes.c_int64)]
+                ("updates", ctypes.c_int64), ("tail_ms", ctypes.c_double)]
 
 
 class VlError(RuntimeError):

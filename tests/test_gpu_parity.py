@@ -189,6 +189,7 @@ def test_mass_conservation_and_moments():
     g.translate(0.1, "xyz", 5, check=True)
     assert abs(g.mass() - m0) <= MASS_TOL * m0
     s = g.stats()
+    assert 0.0 < s.tail_ms < s.sweep_ms  # the persistent kernel's idle tail, fused steps
     assert s.steps == 5 and s.dropped_blocks == 0 and abs(s.mass - m0) <= MASS_TOL * m0
 
 
