@@ -71,11 +71,16 @@ typedef enum {
 typedef enum {
     VL_FORM_FUSED = 0,  /* Ghost Translation: one tile+halo load, x->y->z in one kernel */
     VL_FORM_3PASS = 1,  /* classical: one HBM round trip per sweep direction */
-    VL_FORM_AUTO = 2    /* pick per workload: the first steps of the first call for a
-                           workload probe each form (they compute the same result) and
-                           the fastest is cached per workload key for later calls; with
-                           the environment variable VLGT_TUNE_CACHE naming a file the
-                           choices also persist across processes (JSON lines) */
+    VL_FORM_AUTO = 2    /* pick per workload: the first steps run for a workload probe
+                           each candidate -- fused with 16-row tiles (orders ending in z),
+                           fused with 8-row tiles, 3-pass (FP32 storage only) -- with one
+                           warm-up and one timed step each, over as many calls as it takes
+                           (every probe step advances the real state; the candidates
+                           compute the same result).  The fastest is cached per workload
+                           key (grid, velocity mesh, order, limiter, storage, slots per
+                           cell rounded to a power of two); with the environment variable
+                           VLGT_TUNE_CACHE naming a file the choices also persist across
+                           processes (JSON lines) */
 } vl_form;
 
 /* Spatial box: n cells per dimension, cell size dx, origin x0 (periodic). */
@@ -116,11 +121,12 @@ typedef struct {
     int tile[2];    /* fused tile extent along the first two sweep axes; 0 = default */
     int check;      /* 1: synchronise after the call and report device-side errors */
     int graph;      /* 1: run the nsteps steps as one captured CUDA graph with no host
-                       synchronisation between steps (the graph is cached and replayed
-                       by later calls with the same arguments); the pools are sized to
-                       `capacity` blocks beforehand, a step that would need more is
-                       detected on the device, the state stays at the last complete
-                       step, the capacity grows and the remaining steps run again */
+                       synchronisation between steps.  The pools are sized to at least
+                       `capacity` blocks beforehand (they never shrink); a step that
+                       would need more slots than they hold is detected on the device,
+                       the state stays at the last complete step, the pools grow and
+                       the remaining steps run again.  The graph is cached and replayed
+                       by later calls with the same step count, form, order and pools. */
     int reserved0;
     int64_t capacity; /* graph mode: blocks per layout; 0 = 1.25 x the current slots */
     int reserved[4];
