@@ -262,6 +262,96 @@ struct Walk {
     }
 };
 
+// Packed FP32 pairs (sm_100 family f32x2 instructions): each lane is rounded exactly as
+// the scalar add.rn / mul.rn / fma.rn, so two walks packed into one float2 give the bits
+// of two scalar walks with half the floating-point instructions.
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "add.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "sub.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "mul.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{.reg .b64 x, y, z, w;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "mov.b64 z, {%6, %7};\n\tfma.rn.f32x2 w, x, y, z;\n\tmov.b64 {%0, %1}, w;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+struct WalkConst2 {
+    float2 g, A, B;
+};
+
+__device__ __forceinline__ WalkConst2 pack_const(const WalkConst& p, const WalkConst& q)
+{
+    return {make_float2(p.g, q.g), make_float2(p.A, q.A), make_float2(p.B, q.B)};
+}
+
+// Two Walks in lock step, lanes .x and .y; both must walk the same way.  Every
+// operation is the one Walk::push performs, in the same order, per lane.
+template <bool kLimiter>
+struct Walk2 {
+    float2 a1, a2, l1, l2, d0, o3;
+
+    __device__ __forceinline__ void reset()
+    {
+        a1 = a2 = l1 = l2 = d0 = o3 = make_float2(0.0f, 0.0f);
+    }
+
+    __device__ __forceinline__ float2 push(float2 a, const WalkConst2& k)
+    {
+        const float2 half = make_float2(0.5f, 0.5f), twelfth = make_float2(1.0f / 12.0f, 1.0f / 12.0f);
+        float2 dn = sub2(a, a1);
+        float2 e = fma2(sub2(l2, dn), twelfth, mul2(half, l1));
+        float2 d1, out;
+        if (kLimiter) {
+            d1.x = copysignf(fmaxf(min_xorsign_abs(e.x, l1.x), 0.0f), l1.x);
+            d1.y = copysignf(fmaxf(min_xorsign_abs(e.y, l1.y), 0.0f), l1.y);
+            const float2 dd0 = add2(d0, d0), dd1 = add2(d1, d1);
+            const float2 u = make_float2(min_xorsign_abs(d1.x, dd0.x), min_xorsign_abs(d1.y, dd0.y));
+            const float2 w = make_float2(min_xorsign_abs(d0.x, dd1.x), min_xorsign_abs(d0.y, dd1.y));
+            float2 xm = fma2(k.A, u, mul2(k.B, w));
+            xm.x = copysignf(fmaxf(xm.x, 0.0f), d1.x);
+            xm.y = copysignf(fmaxf(xm.y, 0.0f), d1.y);
+            out = fma2(k.g, a2, xm);
+        } else {
+            d1 = e;
+            out = fma2(k.B, d0, fma2(k.A, d1, mul2(k.g, a2)));
+        }
+        float2 res = add2(sub2(a2, out), o3);
+        d0 = sub2(l1, d1);
+        a2 = a1;
+        a1 = a;
+        l2 = l1;
+        l1 = dn;
+        o3 = out;
+        return res;
+    }
+};
+
 // Slot (rank) of cell (x, row) of block id b in a layout, or -1 when the cell has no
 // slot.  With check_keep the cell must also hold the block (kbits).
 __device__ __forceinline__ int64_t cell_rank(const LayoutView& L, const GridGeom& G, int b,

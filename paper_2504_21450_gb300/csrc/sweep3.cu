@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
         kc[i] = walk_const((P.vmin + (iv + 0.5) * P.dv) * P.cs);
     }
     const bool up = kc[0].up != 0;
+    const WalkConst2 kp[2] = {pack_const(kc[0], kc[1]), pack_const(kc[2], kc[3])};
     const bool uni = __all_sync(0xffffffffu, up) || __all_sync(0xffffffffu, !up);
 
     const T* src = static_cast<const T*>(P.in.pool) +
@@ -306,17 +307,21 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
     load(0, t0);
     load(1 % nd, t1);
 
-    Walk<kLim> s[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) s[i].reset();
+    Walk2<kLim> s[2];  // cells (0, 1) and (2, 3) of the row, packed
+    s[0].reset();
+    s[1].reset();
     float msum = 0.0f;
     float vmx = 0.0f;
     double mass = 0.0;
     const float thr = P.thr;
     auto push_emit = [&](int m, const float (&a)[4]) {
         float res[4];
-#pragma unroll
-        for (int i = 0; i < 4; i++) res[i] = s[i].push(a[i], kc[i]);
+        const float2 r01 = s[0].push(make_float2(a[0], a[1]), kp[0]);
+        const float2 r23 = s[1].push(make_float2(a[2], a[3]), kp[1]);
+        res[0] = r01.x;
+        res[1] = r01.y;
+        res[2] = r23.x;
+        res[3] = r23.y;
         if (m < 2) return;
         const int c = cell_at(m - 2);
         const int r = rout[c];
@@ -347,8 +352,8 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
     for (; m < 0; m++) {
         float a[4];
         load(wrapi(m, nd), a);
-#pragma unroll
-        for (int i = 0; i < 4; i++) s[i].push(a[i], kc[i]);
+        s[0].push(make_float2(a[0], a[1]), kp[0]);
+        s[1].push(make_float2(a[2], a[3]), kp[1]);
     }
     for (; m + kBatch4 <= nd; m += kBatch4) {
         float a[kBatch4][4];
