@@ -143,6 +143,8 @@ def step_field(f, c, order: str = "xyz", limiter: bool = True, periodic: bool = 
 
 def step_field_gt(f, c, order: str = "xyz", limiter: bool = True, k: int = 3,
                   box=(4, 4, 4)) -> np.ndarray:
+    """GT-k tiled step (Section 3.2) with boxes of extents box (x, y, z); an extent of 0
+    makes the boxes span that whole periodic axis, with no ghost layer along it."""
     out = np.array(f, dtype=np.float64, order="C", copy=True)
     cc = np.ascontiguousarray(c, dtype=np.float64)
     _check(lib().vlref_step_field_gt(_ptr(_dims(out)), _ptr(out), _ptr(cc),

@@ -272,12 +272,35 @@ static void gt_update_halfwidths(int k, const int order[3], int hw[3][3])
  * layer of 3 cells per side from the pre-step field in one go (the single coalesced
  * ghost update of Section 3), runs the three sweeps on its update regions only (cells
  * outside keep the values they were loaded with, Section 3.2), and writes its local
- * cells back.  Boxes that do not divide the grid are ragged at the high end. */
+ * cells back.  Boxes that do not divide the grid are ragged at the high end.
+ * box[d] = 0 makes every box span the whole periodic axis d with no neighbour along
+ * it: all cells along d are local, so its ghost layer only mirrors the box's own
+ * cells and is refreshed from them after every sweep (a domain that wraps onto itself
+ * has nothing to exchange along that axis). */
+static void refresh_wrapped_ghosts(double* buf, const long e[3], const long ext[3], int d, int H)
+{
+    long pos[3];
+    for (pos[2] = 0; pos[2] < e[2]; pos[2]++)
+        for (pos[1] = 0; pos[1] < e[1]; pos[1]++)
+            for (pos[0] = 0; pos[0] < e[0]; pos[0]++) {
+                long t = pos[d] - H;
+                if (t >= 0 && t < ext[d]) continue;
+                long src[3] = {pos[0], pos[1], pos[2]};
+                src[d] = ((t % ext[d]) + ext[d]) % ext[d] + H;
+                buf[pos[0] + e[0] * (pos[1] + e[1] * pos[2])] = buf[src[0] + e[0] * (src[1] + e[1] * src[2])];
+            }
+}
+
 int vlref_step_field_gt(const int n[3], double* f, const double c[3], const int order[3],
-                        int limiter, int k, const int box[3])
+                        int limiter, int k, const int box_in[3])
 {
     if (!n || n[0] <= 0 || n[1] <= 0 || n[2] <= 0 || !valid_order(order)) return 1;
-    if (k < 1 || k > 3 || !box || box[0] <= 0 || box[1] <= 0 || box[2] <= 0) return 1;
+    if (k < 1 || k > 3 || !box_in || box_in[0] < 0 || box_in[1] < 0 || box_in[2] < 0) return 1;
+    int box[3], whole[3];
+    for (int d = 0; d < 3; d++) {
+        whole[d] = box_in[d] == 0;
+        box[d] = whole[d] ? n[d] : box_in[d];
+    }
     for (int d = 0; d < 3; d++)
         if (fabs(c[d]) > 1.0) return 2;
     const int H = 3;
@@ -343,6 +366,8 @@ int vlref_step_field_gt(const int n[3], double* f, const double c[3], const int 
                     double* sw = buf;
                     buf = nxt;
                     nxt = sw;
+                    for (int q = 0; q < 3; q++)
+                        if (whole[q]) refresh_wrapped_ghosts(buf, e, ext, q, H);
                 }
                 for (long z = 0; z < ext[2]; z++)
                     for (long y = 0; y < ext[1]; y++)

@@ -47,6 +47,8 @@ int vlref_sweep_field(const int n[3], int periodic, const double* in, double* ou
                       int dim, double c, int limiter);
 int vlref_step_field(const int n[3], int periodic, double* f, const double c[3],
                      const int order[3], int limiter);
+/* GT-k (k = 1..3) tiled step with boxes of extents box[]; box[d] = 0: every box spans
+ * the whole periodic axis d and has no ghosts along it. */
 int vlref_step_field_gt(const int n[3], double* f, const double c[3], const int order[3],
                         int limiter, int k, const int box[3]);
 
