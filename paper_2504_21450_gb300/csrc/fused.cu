@@ -453,10 +453,14 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         };
 
         const bool cvalid = ci < e0;
-        Walk<kLim> zu[kZUni ? L : 1];
+        // streamed windows: with one walking direction per item, rows (2i, 2i+1) share a
+        // packed pair (their velocity cell, hence their constants, is the same)
+        static_assert(L % 2 == 0, "packed streamed windows pair the rows of a segment");
+        Walk2<kLim> zu[kZUni ? L / 2 : 1];
         Slide<kLim> zg[kZUni ? 1 : L];
+        const WalkConst2 kz = pack_const(kw[2], kw[2]);
 #pragma unroll
-        for (int j = 0; j < (kZUni ? L : 1); j++) zu[j].reset();
+        for (int j = 0; j < (kZUni ? L / 2 : 1); j++) zu[j].reset();
 #pragma unroll
         for (int j = 0; j < (kZUni ? 1 : L); j++) zg[j].reset();
         float msum = 0.0f, mcomp = 0.0f;  // Kahan-compensated FP32 mass of this thread
@@ -514,10 +518,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             const int* orow = orank + (s & 3) * TX * TY + j0 * TX + ci;
             float psum = 0.0f;
             unsigned kmask = 0;
-            auto consume = [&](int jj, float yv) {
-                float res;
-                if (kZUni) res = zu[kZUni ? jj : 0].push(yv, kw[2]);
-                else res = zg[kZUni ? 0 : jj].push(yv, ks2);
+            auto emit = [&](int jj, float res) {
                 if (kEmit) {
                     const T code = C::enc(res, inv_out);
                     if (kCodec) {
@@ -543,6 +544,30 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     if (res >= P.thr) kmask |= 1u << jj;
                 }
             };
+            // sweep-1 output of row jj into its streamed window; rows are produced in
+            // walking order (ascending when kUp), and a packed pair is pushed once both
+            // of its rows are in, then emitted in that same order
+            float pend = 0.0f;
+            auto consume = [&](int jj, float yv, auto up_tag) {
+                constexpr bool kUp = decltype(up_tag)::value;
+                if constexpr (kZUni) {
+                    if ((jj & 1) == (kUp ? 0 : 1)) {
+                        pend = yv;  // first row of its pair
+                        return;
+                    }
+                    const int lo = kUp ? jj - 1 : jj;
+                    const float2 r = zu[lo >> 1].push(kUp ? make_float2(pend, yv) : make_float2(yv, pend), kz);
+                    if (kUp) {
+                        emit(lo, r.x);
+                        emit(lo + 1, r.y);
+                    } else {
+                        emit(lo + 1, r.y);
+                        emit(lo, r.x);
+                    }
+                } else {
+                    emit(jj, zg[jj].push(yv, ks2));
+                }
+            };
             const float* line = xbuf + (s & 1) * S::XBUF + (j0 * XROW) + ci * NV + v;
             Walk<kLim> wk;
             wk.reset();
@@ -550,13 +575,13 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 #pragma unroll
                 for (int t = 0; t < L + 5; t++) {
                     float r = wk.push(line[t * XROW], kw[1]);
-                    if (t >= 5) consume(t - 5, r);
+                    if (t >= 5) consume(t - 5, r, std::true_type{});
                 }
             } else {
 #pragma unroll
                 for (int t = 0; t < L + 5; t++) {
                     float r = wk.push(line[(L + 5 - t) * XROW], kw[1]);
-                    if (t >= 5) consume(L + 4 - t, r);
+                    if (t >= 5) consume(L + 4 - t, r, std::false_type{});
                 }
             }
             if (kEmit) {
