@@ -348,23 +348,24 @@ def run_ours(args, cfg):
     if form == vlasov.VL_FORM_AUTO:
         # the autotuner's probe steps (one warm-up and one timed step per candidate),
         # before and apart from the warm-up below
-        g.translate(cfg.dt, args.order, 6, form)
+        g.translate(cfg.dt, args.order, 6, form, ghost=args.ghost)
         st = g.stats()
         tune = {"ms_per_step": dict(zip(["fused16", "fused8", "3pass"], [round(x, 3) for x in st.tune_ms])),
                 "chosen": {vlasov.VL_FORM_FUSED: "fused", vlasov.VL_FORM_3PASS: "3pass"}.get(st.form_used),
                 "tile_rows": int(st.tile_rows_used)}
     if args.graph:
         # warm-up with the same step count, so that the timed call replays a cached graph
-        g.translate(cfg.dt, args.order, chunk, form, graph=True, capacity=capacity_for_call())
+        g.translate(cfg.dt, args.order, chunk, form, graph=True, capacity=capacity_for_call(),
+                    ghost=args.ghost)
         if args.presize == "fixed":
             cap = max(cap, g.stats().capacity)
         for _ in range(max(0, args.warmup - 1)):
-            g.translate(cfg.dt, args.order, 1, form)
+            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost)
         caps.clear()
         cap_ms.clear()
     else:
         for _ in range(args.warmup):
-            g.translate(cfg.dt, args.order, 1, form)
+            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
@@ -381,7 +382,7 @@ def run_ours(args, cfg):
         ev0.record(stream)
         for n in step_calls:
             g.translate(cfg.dt, args.order, n, form, graph=args.graph,
-                        capacity=capacity_for_call() if args.graph else 0)
+                        capacity=capacity_for_call() if args.graph else 0, ghost=args.ghost)
             s = g.stats()
             updates += s.updates
             sweep_ms += s.sweep_ms
@@ -415,7 +416,7 @@ def run_ours(args, cfg):
         for _ in range(e_steps):
             vlasov.vl_set_blocks(g.handle, nb, h_off.data_ptr(), h_ids.data_ptr(), h_vals.data_ptr(), 0)
             e_updates += nb * 64
-            g.translate(cfg.dt, args.order, 1, form)
+            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost)
             _ = g.stats().mass
         torch.cuda.synchronize()
         e_el = time.perf_counter() - t0
@@ -439,6 +440,8 @@ def run_ours(args, cfg):
     bytes_per_update = BYTES_PER_UPDATE[form_used] * STORAGE_BYTES[args.storage] / 4
     achieved = bytes_per_update * per_launch_updates / avg_launch_s / 1e9
     workload = cfg.name if args.storage == "f32" else f"{cfg.name}-{args.storage}"
+    if args.ghost != 3:
+        workload += f"-gt{args.ghost}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "kernel": KERNEL[form_used],
@@ -451,6 +454,7 @@ def run_ours(args, cfg):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(cfg),
                    "form": form_used, "storage": args.storage, "order": args.order, "parallelism": f"replicas{world}",
+                   "ghost": args.ghost,
                    "graph": bool(args.graph), "capacity_regrows": regrows,
                    "l2": f"state ({updates / args.steps * STORAGE_BYTES[args.storage] / 1e9:.1f} GB per copy) larger than L2; no flush",
                    "blocks_per_step": updates / args.steps / 64},
@@ -484,6 +488,9 @@ def main():
     ap.add_argument("--form", default="auto", choices=["fused", "3pass", "auto"],
                     help="auto: the library's autotuner times the fused form (16- and 8-row "
                          "tiles) and the 3-pass form on this workload and keeps the fastest")
+    ap.add_argument("--ghost", type=int, default=3, choices=[1, 2, 3],
+                    help="GT-k ghost depth of the fused form: 3 is exact, 1 and 2 are the reduced "
+                         "(approximate) GT1 and GT2 of Section 3.2")
     ap.add_argument("--graph", action="store_true",
                     help="run the timed steps as one captured CUDA graph (no host sync per step)")
     ap.add_argument("--config", default="uniform", choices=sorted(inputs.CONFIGS))
@@ -499,6 +506,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="steps per captured call (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.ghost != 3 and args.form != "fused":
+        ap.error("--ghost 1 or 2 needs --form fused (GT1/GT2 exist in the fused form only)")
     cfg = inputs.CONFIGS[args.config]
     if args.grid:
         import dataclasses

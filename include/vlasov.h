@@ -117,7 +117,15 @@ typedef struct {
     int limiter;    /* 1 (default): monotonicity limiter on; 0: linear PPM (dense
                        velocity meshes only: without the limiter content can reach
                        cells outside the 27-cell block union) */
-    int ghost;      /* ghost-layer depth k of GT-k; only 3 (exact) is implemented */
+    int ghost;      /* ghost depth k of GT-k (Section 3.2), default 3.  3 (GT3) is exact:
+                       the step equals the classical sweep-by-sweep one.  1 and 2 (GT1,
+                       GT2) exist in the fused form with FP32 storage (else VL_EINVAL):
+                       the first sweep runs only on the tile's rows and the k rows
+                       beyond it on each side along the second sweep axis; rows further
+                       out enter the second sweep's stencils with their pre-step values,
+                       so the result is approximate and its error depends on the tile
+                       shape (16 x `tile[1]` cells along the first two sweep axes, the
+                       third axis whole) */
     int tile[2];    /* fused tile extent along the first two sweep axes; 0 = default */
     int check;      /* 1: synchronise after the call and report device-side errors */
     int graph;      /* 1: run the nsteps steps as one captured CUDA graph with no host

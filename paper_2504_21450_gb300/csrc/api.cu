@@ -291,7 +291,7 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
                                   (uint64_t)(uintptr_t)g->lay[0].pool, (uint64_t)(uintptr_t)g->lay[1].pool,
                                   (uint64_t)(uintptr_t)g->step_ctr, (uint64_t)(uintptr_t)g->items,
                                   (uint64_t)(uintptr_t)a.walk, (uint64_t)(uintptr_t)g->stream,
-                                  (uint64_t)a.tile[1]};
+                                  (uint64_t)a.tile[1], (uint64_t)a.ghost};
         for (uint64_t v : parts) key = mix(key, v);
         if (!g->graph_exec || key != g->graph_key) {
             if (g->graph_exec) {
@@ -811,8 +811,12 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
         return fail(g, VL_EINVAL, "vl_translate: dt must be finite and >= 0, nsteps >= 0");
     if (opts.form != VL_FORM_FUSED && opts.form != VL_FORM_3PASS && opts.form != VL_FORM_AUTO)
         return fail(g, VL_EINVAL, "vl_translate: unknown form");
-    if (opts.ghost != 3)
-        return fail(g, VL_EINVAL, "vl_translate: only the exact ghost depth 3 (GT3) is implemented");
+    if (opts.ghost < 1 || opts.ghost > 3)
+        return fail(g, VL_EINVAL, "vl_translate: ghost depth must be 1, 2 or 3");
+    if (opts.ghost != 3 && opts.form != VL_FORM_FUSED)
+        return fail(g, VL_EINVAL, "vl_translate: GT1 and GT2 exist in the fused form only");
+    if (opts.ghost != 3 && g->codec != 0)
+        return fail(g, VL_EINVAL, "vl_translate: GT1 and GT2 are built for FP32 storage only");
     if (!g->has_state) return fail(g, VL_ESTATE, "vl_translate: no state (call vl_set_blocks first)");
     // Section 2.1: dt keeps every velocity cell within one face neighbour per sweep
     for (int d = 0; d < 3; d++) {
@@ -848,6 +852,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
     a.limiter = opts.limiter ? 1 : 0;
     a.tile[0] = opts.tile[0];
     a.tile[1] = opts.tile[1];
+    a.ghost = opts.ghost;
     if (!g->ev_sweep0) {
         cudaEventCreate(&g->ev_sweep0);
         cudaEventCreate(&g->ev_sweep1);

@@ -76,6 +76,7 @@ struct FusedArgs {
     int report_late;     // testing hook: a staging wait that is not complete at its first
                          // poll is reported as overdue (VL_ETIMEOUT), then waited for
     uint64_t* cta_done;  // optional [gridDim.x]: %globaltimer when the CTA ran out of work
+    int gt_k;            // ghost depth of GT-k, 1..3 (3: exact)
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
@@ -154,7 +155,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 constexpr unsigned kMaxPolls = 1u << 24;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
-template <int TY, bool kLim, bool kZUni, int kCodec>
+template <int TY, bool kLim, bool kZUni, int kCodec, bool kRed = false>
 __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 {
     using C = Codec<kCodec>;
@@ -230,6 +231,12 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         const bool bulk = dense_in && a0 == 0;  // halo rows are contiguous runs in HBM
         const bool sbulk = !dense_in && a0 == 0;  // sparse rows: runs of present cells
         const bool full = e0 == TX && e1 == TY;
+        // GT-k (Section 3.2): sweep 0 runs on the halo rows within k of the tile along
+        // axis 1 (with k = 3, every row a sweep-1 stencil of the tile reads).  In the
+        // reduced variants (kRed: k = 1, 2) the other rows walk with c = 0, which
+        // returns every value unchanged (no outflow, and a - (+-0) + (+-0) = a), so
+        // they enter sweep 1 with their pre-step values
+        const bool x_active = hi - H >= -P.gt_k && hi - H < e1 + P.gt_k;
         const int64_t ibase = ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * NV;
         const int64_t obase = ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * NV;
         const int64_t okeep = (int64_t)P.out.base[b];
@@ -282,6 +289,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 ks2 = SweepConst{s4.x, s4.y, s4.z, s4.w != 0.0f ? 1 : 0};
             }
         }
+        const WalkConst kx = (!kRed || x_active) ? kw[0] : WalkConst{0.0f, 0.0f, 0.0f, kw[0].up};
         const bool zup = kw[2].up != 0;  // uniform over the item when kZUni
         // streamed plane of step s and the output plane it completes
         auto plane_of = [&](int s) { return kZUni ? (zup ? s - H : n2 + 2 - s) : s - H; };
@@ -491,13 +499,13 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 if (kw[0].up) {
 #pragma unroll
                     for (int t = 0; t < TX + 5; t++) {
-                        float r = wk.push(C::dec(line[t * NV], sc_in), kw[0]);
+                        float r = wk.push(C::dec(line[t * NV], sc_in), kx);
                         if (t >= 5) xo[(t - 5) * NV] = r;
                     }
                 } else {
 #pragma unroll
                     for (int t = 0; t < TX + 5; t++) {
-                        float r = wk.push(C::dec(line[(TX + 5 - t) * NV], sc_in), kw[0]);
+                        float r = wk.push(C::dec(line[(TX + 5 - t) * NV], sc_in), kx);
                         if (t >= 5) xo[(TX + 4 - t) * NV] = r;
                     }
                 }
@@ -675,10 +683,10 @@ __global__ void k_tile_items(int64_t ntiles, int nb, const uint32_t* __restrict_
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-template <int TY, bool kLim, bool kZUni, int kCodec = 0>
+template <int TY, bool kLim, bool kZUni, int kCodec = 0, bool kRed = false>
 vl_status launch_fused(Grid* g, const FusedArgs& P)
 {
-    auto kern = k_fused<TY, kLim, kZUni, kCodec>;
+    auto kern = k_fused<TY, kLim, kZUni, kCodec, kRed>;
     const int smem = Shape<TY, (int)sizeof(typename Codec<kCodec>::T)>::SMEM;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int nsm = 0, per_sm = 0;
@@ -774,17 +782,28 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     P.ctr = a.ctr;
     P.report_late = fault_requested("timeout") ? 1 : 0;
     P.cta_done = a.stamp_ctas ? g->cta_done : nullptr;
+    P.gt_k = a.ghost;
     record_sweep_event(a.ev0, g->stream, a.ev_node);
     vl_status st = VL_OK;
-    with_codec(g->codec, [&](auto c) {
-        constexpr int kc = decltype(c)::value;
+    if (a.ghost != 3) {
+        // reduced ghost depth: compiled for FP32 storage only (the host checks)
         if (zuni && ty == 16)
-            st = a.limiter ? launch_fused<16, true, true, kc>(g, P) : launch_fused<16, false, true, kc>(g, P);
+            st = a.limiter ? launch_fused<16, true, true, 0, true>(g, P) : launch_fused<16, false, true, 0, true>(g, P);
         else if (zuni)
-            st = a.limiter ? launch_fused<8, true, true, kc>(g, P) : launch_fused<8, false, true, kc>(g, P);
+            st = a.limiter ? launch_fused<8, true, true, 0, true>(g, P) : launch_fused<8, false, true, 0, true>(g, P);
         else
-            st = a.limiter ? launch_fused<8, true, false, kc>(g, P) : launch_fused<8, false, false, kc>(g, P);
-    });
+            st = a.limiter ? launch_fused<8, true, false, 0, true>(g, P) : launch_fused<8, false, false, 0, true>(g, P);
+    } else {
+        with_codec(g->codec, [&](auto c) {
+            constexpr int kc = decltype(c)::value;
+            if (zuni && ty == 16)
+                st = a.limiter ? launch_fused<16, true, true, kc>(g, P) : launch_fused<16, false, true, kc>(g, P);
+            else if (zuni)
+                st = a.limiter ? launch_fused<8, true, true, kc>(g, P) : launch_fused<8, false, true, kc>(g, P);
+            else
+                st = a.limiter ? launch_fused<8, true, false, kc>(g, P) : launch_fused<8, false, false, kc>(g, P);
+        });
+    }
     record_sweep_event(a.ev1, g->stream, a.ev_node);
     return st;
 }
@@ -817,6 +836,7 @@ vl_status launch_fused_dense(const GridGeom& G, const LayoutView& in, const Layo
     P.ctr = ctr;
     P.report_late = 0;
     P.cta_done = nullptr;
+    P.gt_k = 3;
     Grid tmp;  // launch helper needs the device and the stream only
     tmp.dev.device = device;
     tmp.stream = stream;

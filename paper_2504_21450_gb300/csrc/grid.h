@@ -146,6 +146,7 @@ struct StepArgs {
     int order[3];       // physical axis of sweep j
     int limiter;
     int tile[2];
+    int ghost = 3;        // GT-k ghost depth (fused form; 3 = exact)
     const float4* walk;   // device [3][nvmax]: WalkConst per axis and velocity index
     const float4* sweep;  // device [3][nvmax]: SweepConst per axis and velocity index
     int nvmax;

@@ -368,9 +368,10 @@ class Grid:
 
     def translate(self, dt: float, order: str = "xyz", nsteps: int = 1, form: int = VL_FORM_FUSED,
                   limiter: bool = True, check: bool = False, graph: bool = False, capacity: int = 0,
-                  tile_rows: int = 0):
+                  tile_rows: int = 0, ghost: int = 3):
         o = vl_translate_opts_default()
         o.tile[1] = int(tile_rows)
+        o.ghost = int(ghost)
         o.form = int(form)
         o.limiter = int(bool(limiter))
         o.check = int(bool(check))

@@ -27,11 +27,12 @@ def block_keys(off, ids):
 
 
 def compare_step(mesh, before: oracle.Blocks, gpu_after, threshold, dt, order="xyz",
-                 limiter=True, cells=None):
+                 limiter=True, cells=None, gt_k=0, gt_box=(4, 4, 4)):
     """One oracle step from `before`, compared with the GPU's result (off, ids, vals).
-    `cells` restricts the comparison to a subset of cell indices (windowed parity).
+    `cells` restricts the comparison to a subset of cell indices (windowed parity);
+    gt_k > 0 takes the oracle's tiled GT-k step with boxes gt_box.
     Returns (max abs error, max |f| of the oracle, ambiguous blocks, oracle blocks, stats)."""
-    ref, st, u, keep = oracle.step(mesh, before, dt, threshold, order, limiter)
+    ref, st, u, keep = oracle.step(mesh, before, dt, threshold, order, limiter, gt_k, gt_box)
     if limiter:
         assert st.leaked == 0.0
     off, ids, vals = gpu_after
