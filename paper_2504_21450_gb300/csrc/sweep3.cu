@@ -359,6 +359,20 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
         float a[kBatch4][4];
 #pragma unroll
         for (int u = 0; u < kBatch4; u++) load(m + u, a[u]);
+        // L2 prefetch of the next batch (one lane per 64-byte chunk row): DRAM keeps
+        // working while this batch's arithmetic runs, and the next loads hit L2.  It
+        // takes no registers; a distance of one batch measured best (0.88 of the copy
+        // bandwidth against 0.76 without, 0.85 at two batches)
+        if (vy == 0) {
+#pragma unroll
+            for (int u = 0; u < kBatch4; u++) {
+                const int pm = m + kBatch4 + u;
+                if (pm < nd) {
+                    const int r = rin[cell_at(pm)];
+                    if (r >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (int64_t)r * kChunk));
+                }
+            }
+        }
 #pragma unroll
         for (int u = 0; u < kBatch4; u++) push_emit(m + u, a[u]);
         if (P.last) {
