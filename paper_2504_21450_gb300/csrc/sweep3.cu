@@ -359,11 +359,13 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
         float a[kBatch4][4];
 #pragma unroll
         for (int u = 0; u < kBatch4; u++) load(m + u, a[u]);
-        // L2 prefetch of the next batch (one lane per 64-byte chunk row): DRAM keeps
-        // working while this batch's arithmetic runs, and the next loads hit L2.  It
-        // takes no registers; a distance of one batch measured best (0.88 of the copy
-        // bandwidth against 0.76 without, 0.85 at two batches)
-        if (vy == 0) {
+        // L2 prefetch of the next batch (one lane per chunk row): DRAM keeps working
+        // while this batch's arithmetic runs, and the next loads hit L2.  It takes no
+        // registers; a distance of one batch measured best (FP32: 0.88 of the copy
+        // bandwidth against 0.76 without, 0.85 at two batches).  16-bit storage moves
+        // half the bytes and is issue-bound, where the extra instructions cost more
+        // than the overlap gains (46.9 against 44.4 ms per step), so it goes without.
+        if (kCodec == 0 && vy == 0) {
 #pragma unroll
             for (int u = 0; u < kBatch4; u++) {
                 const int pm = m + kBatch4 + u;
