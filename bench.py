@@ -11,7 +11,7 @@ Metric: phase-space cell updates per second (one update = one velocity cell of o
 spatial cell advanced through the full x->y->z step), whole job.  The state (34 GB)
 is far larger than L2 (129 MB), so no L2 flush is needed between steps.
 
---impl reference times the FP64 CPU oracle on the box's host cores instead, on a
+--impl reference times the FP64 CPU oracle on the machine's host cores instead, on a
 bounded window of the same workload.
 """
 from __future__ import annotations
