@@ -28,6 +28,7 @@ struct PassArgs {
     LayoutView in, out;
     int dim;            // physical axis of this pass
     int check_keep_in;  // 1: read only present blocks of `in`
+    int in_is_out;      // 1: `in` and `out` are the same layout (passes 2 and 3, in place)
     double cs;          // dt / dx_dim
     double vmin, dv;    // velocity mesh along dim
     int last;           // last pass: keep flags and mass
@@ -248,8 +249,10 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
     const int nd = G.n[P.dim];
     const int64_t npen = G.N / nd;
     if (P.out.cnt[b] == 0) return;
+    // passes 2 and 3 work in place (check_keep_in = 0): input and output ranks are the
+    // same table
     int* s_rin = s_rank4;
-    int* s_rout = s_rank4 + kPen4 * nd;
+    int* s_rout = P.in_is_out ? s_rank4 : s_rank4 + kPen4 * nd;
 
     if (threadIdx.x < kPen4) s_any[threadIdx.x] = 0;
     __syncthreads();
@@ -261,11 +264,11 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
             int x;
             int64_t row;
             pencil_cell(G, P.dim, p, i, x, row);
-            ri = (int)cell_rank(P.in, G, b, x, row, P.check_keep_in != 0);
             ro = (int)cell_rank(P.out, G, b, x, row, false);
+            ri = P.in_is_out ? ro : (int)cell_rank(P.in, G, b, x, row, P.check_keep_in != 0);
         }
         s_rin[k * nd + i] = ri;
-        s_rout[k * nd + i] = ro;
+        if (!P.in_is_out) s_rout[k * nd + i] = ro;
         if (ro >= 0) s_any[k] = 1;
     }
     __syncthreads();
@@ -419,6 +422,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         P.out = B.view();
         P.dim = d;
         P.check_keep_in = j == 0 ? 1 : 0;
+        P.in_is_out = j == 0 ? 0 : 1;
         P.cs = a.c_scale[d];
         P.vmin = g->vmesh.vmin[d];
         P.dv = g->vmesh.dv[d];
