@@ -80,7 +80,8 @@ typedef enum {
                            key (grid, velocity mesh, order, limiter, storage, slots per
                            cell rounded to a power of two); with the environment variable
                            VLGT_TUNE_CACHE naming a file the choices also persist across
-                           processes (JSON lines) */
+                           processes (JSON lines).  Exact forms only: it requires
+                           ghost = 3 */
 } vl_form;
 
 /* Spatial box: n cells per dimension, cell size dx, origin x0 (periodic). */
