@@ -151,9 +151,20 @@ def cpu_baseline(cfg, budget_s=20.0):
         if time.perf_counter() - t0 >= budget_s * 0.5 or reps >= 20:
             break
     el = time.perf_counter() - t0
+    # the same oracle on one core, on an 8^3-cell window (one step)
+    small = (8, 8, 8)
+    init1 = inputs.generate(cfg, size=small, thr=thr)
+    mesh1 = oracle.Mesh(n=small, nv=cfg.nv, vmin=cfg.vmin, dv=cfg.dv, dx=cfg.dx)
+    blk1 = oracle.as_blocks(init1.off, init1.ids, init1.vals.astype(np.float64))
+    t1 = time.perf_counter()
+    oracle.step(mesh1, blk1, cfg.dt, thr, "xyz", nthreads=1)
+    single = blk1.nblocks * 64 / (time.perf_counter() - t1)
     return {"value": updates / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} step(s) of a periodic 16^3-cell window x {cfg.nv[0]}^3 velocity "
-                      f"cells ({blk.nblocks * 64:.3g} updates/step), FP64, OpenMP over block ids"}
+                      f"cells ({blk.nblocks * 64:.3g} updates/step), FP64, OpenMP over block ids",
+            "single_core": {"value": single, "unit": UNIT,
+                            "sample": f"1 step of a periodic 8^3-cell window "
+                                      f"({blk1.nblocks * 64:.3g} updates), FP64, one thread"}}
 
 
 def aggregate(el_ms: float, updates: float, dist=None, device="cuda"):

@@ -31,5 +31,6 @@ def test_bench_line_on_the_tiny_workload():
     assert d["e2e"]["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     cpu = d["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
+    assert cpu["single_core"]["value"] > 0
     assert d["autotune"]["chosen"] == d["config"]["form"]
     assert "workload" in d["config"] and d["config"]["workload"].startswith("tiny")
