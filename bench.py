@@ -36,7 +36,8 @@ METRIC = "phase-space cell updates/s (xyz)"
 UNIT = "updates/s"
 BYTES_PER_UPDATE = {"fused": 8.0, "3pass": 8.0}  # per launch, FP32 storage: read f once, write once
 STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}  # bytes per stored value
-KERNEL = {"fused": "k_fused", "3pass": "k_pass"}
+KERNEL = {"fused": "k_gt3", "fused-rows": "k_fused", "3pass": "k_pass"}
+KERNEL_OPT = {"default": 0, "batched": 1, "rows": 2}
 LAUNCHES_PER_STEP = {"fused": 1, "3pass": 3}
 
 
@@ -309,6 +310,7 @@ def run_ours(args, cfg):
             "auto": vlasov.VL_FORM_AUTO}[args.form]
     storage = {"f32": vlasov.VL_STORE_F32, "bf16": vlasov.VL_STORE_BF16_SCALED,
                "f16": vlasov.VL_STORE_F16_SCALED}[args.storage]
+    kern = KERNEL_OPT[args.kernel]
 
     model, train_info = None, None
     if args.presize == "mlp":
@@ -359,24 +361,26 @@ def run_ours(args, cfg):
     if form == vlasov.VL_FORM_AUTO:
         # the autotuner's probe steps (one warm-up and one timed step per candidate),
         # before and apart from the warm-up below
-        g.translate(cfg.dt, args.order, 6, form, ghost=args.ghost)
+        g.translate(cfg.dt, args.order, 8, form, ghost=args.ghost, kernel=kern)
         st = g.stats()
-        tune = {"ms_per_step": dict(zip(["fused16", "fused8", "3pass"], [round(x, 3) for x in st.tune_ms])),
+        tune = {"ms_per_step": dict(zip(["fused_batched", "fused_rows16", "fused_rows8", "3pass"],
+                                        [round(x, 3) for x in st.tune_ms])),
                 "chosen": {vlasov.VL_FORM_FUSED: "fused", vlasov.VL_FORM_3PASS: "3pass"}.get(st.form_used),
+                "kernel": {1: "batched", 2: "rows"}.get(int(st.kernel_used)),
                 "tile_rows": int(st.tile_rows_used)}
     if args.graph:
         # warm-up with the same step count, so that the timed call replays a cached graph
         g.translate(cfg.dt, args.order, chunk, form, graph=True, capacity=capacity_for_call(),
-                    ghost=args.ghost)
+                    ghost=args.ghost, kernel=kern)
         if args.presize == "fixed":
             cap = max(cap, g.stats().capacity)
         for _ in range(max(0, args.warmup - 1)):
-            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost)
+            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost, kernel=kern)
         caps.clear()
         cap_ms.clear()
     else:
         for _ in range(args.warmup):
-            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost)
+            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost, kernel=kern)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
@@ -393,7 +397,7 @@ def run_ours(args, cfg):
         ev0.record(stream)
         for n in step_calls:
             g.translate(cfg.dt, args.order, n, form, graph=args.graph,
-                        capacity=capacity_for_call() if args.graph else 0, ghost=args.ghost)
+                        capacity=capacity_for_call() if args.graph else 0, ghost=args.ghost, kernel=kern)
             s = g.stats()
             updates += s.updates
             sweep_ms += s.sweep_ms
@@ -427,7 +431,7 @@ def run_ours(args, cfg):
         for _ in range(e_steps):
             vlasov.vl_set_blocks(g.handle, nb, h_off.data_ptr(), h_ids.data_ptr(), h_vals.data_ptr(), 0)
             e_updates += nb * 64
-            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost)
+            g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost, kernel=kern)
             _ = g.stats().mass
         torch.cuda.synchronize()
         e_el = time.perf_counter() - t0
@@ -445,6 +449,7 @@ def run_ours(args, cfg):
 
     peak, peak_kind = measured_peak_hbm()
     form_used = {vlasov.VL_FORM_FUSED: "fused", vlasov.VL_FORM_3PASS: "3pass"}.get(stats.form_used, "fused")
+    kernel_key = "fused-rows" if (form_used == "fused" and int(stats.kernel_used) == 2) else form_used
     launches_sweep = LAUNCHES_PER_STEP[form_used] * args.steps
     per_launch_updates = updates / args.steps  # every sweep launch touches every update once
     avg_launch_s = (sweep_ms / launches_sweep) / 1e3 if sweep_ms > 0 else float("nan")
@@ -455,8 +460,8 @@ def run_ours(args, cfg):
         workload += f"-gt{args.ghost}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "kernel": KERNEL[form_used],
-                "traffic": traffic_for(KERNEL[form_used], workload),
+                "kernel": KERNEL[kernel_key],
+                "traffic": traffic_for(KERNEL[kernel_key], workload),
                 "algorithmic_bytes_per_launch": bytes_per_update * per_launch_updates,
                 "avg_launch_ms": avg_launch_s * 1e3}
     line = {
@@ -466,6 +471,7 @@ def run_ours(args, cfg):
         "config": {"workload": workload_name(cfg),
                    "form": form_used, "storage": args.storage, "order": args.order, "parallelism": f"replicas{world}",
                    "ghost": args.ghost,
+                   "kernel": KERNEL[kernel_key],
                    "graph": bool(args.graph), "capacity_regrows": regrows,
                    "l2": f"state ({updates / args.steps * STORAGE_BYTES[args.storage] / 1e9:.1f} GB per copy) larger than L2; no flush",
                    "blocks_per_step": updates / args.steps / 64},
@@ -499,6 +505,8 @@ def main():
     ap.add_argument("--form", default="auto", choices=["fused", "3pass", "auto"],
                     help="auto: the library's autotuner times the fused form (16- and 8-row "
                          "tiles) and the 3-pass form on this workload and keeps the fastest")
+    ap.add_argument("--kernel", default="default", choices=sorted(KERNEL_OPT),
+                    help="fused form: plane-batched kernel, row-segment kernel, or the default choice")
     ap.add_argument("--ghost", type=int, default=3, choices=[1, 2, 3],
                     help="GT-k ghost depth of the fused form: 3 is exact, 1 and 2 are the reduced "
                          "(approximate) GT1 and GT2 of Section 3.2")

@@ -136,7 +136,11 @@ typedef struct {
                        the state stays at the last complete step, the pools grow and
                        the remaining steps run again.  The graph is cached and replayed
                        by later calls with the same step count, form, order and pools. */
-    int reserved0;
+    int kernel;     /* fused form, which kernel: 0 (default) the plane-batched kernel (16 x 16
+                       tiles) where it applies -- FP32 storage, GT3, streamed axis y or z, no
+                       velocity block straddling v_d = 0, tile[1] = 0 -- else the row-segment
+                       kernel; 1 the plane-batched kernel (VL_EINVAL where it does not
+                       apply); 2 the row-segment kernel (tile rows from tile[1]) */
     int64_t capacity; /* graph mode: blocks per layout; 0 = 1.25 x the current slots */
     int reserved[4];
 } vl_translate_opts;
@@ -160,14 +164,17 @@ typedef struct {
     int64_t capacity;       /* graph mode: blocks per layout at the end of the call */
     int form_used;          /* vl_form of the last step (after autotuning) */
     int tile_rows_used;     /* fused form: tile rows along the second sweep axis */
-    double tune_ms[3];      /* autotuner probes (ms per step): fused 16-row tile, fused
-                               8-row tile, 3-pass; 0 = not probed in this call */
+    double tune_ms[4];      /* autotuner probes (ms per step): fused plane-batched kernel,
+                               fused row-segment kernel with 16-row and 8-row tiles,
+                               3-pass; 0 = not probed */
     int64_t updates;        /* phase-space cell updates of the call: velocity cells present
                                at the start of each step, summed over its steps */
     double tail_ms;         /* fused steps run one by one: summed over steps, the time from
                                the first to the last CTA of the persistent sweep kernel
                                running out of work (the single-GPU counterpart of the
                                paper's wait time, Table 1); 0 otherwise */
+    int kernel_used;        /* fused form: 1 plane-batched kernel, 2 row-segment kernel */
+    int reserved_stats;
 } vl_step_stats;
 
 void vl_translate_opts_default(vl_translate_opts* opts);

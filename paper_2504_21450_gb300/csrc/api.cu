@@ -291,7 +291,7 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
                                   (uint64_t)(uintptr_t)g->lay[0].pool, (uint64_t)(uintptr_t)g->lay[1].pool,
                                   (uint64_t)(uintptr_t)g->step_ctr, (uint64_t)(uintptr_t)g->items,
                                   (uint64_t)(uintptr_t)a.walk, (uint64_t)(uintptr_t)g->stream,
-                                  (uint64_t)a.tile[1], (uint64_t)a.ghost};
+                                  (uint64_t)a.tile[1], (uint64_t)a.ghost, (uint64_t)a.kernel};
         for (uint64_t v : parts) key = mix(key, v);
         if (!g->graph_exec || key != g->graph_key) {
             if (g->graph_exec) {
@@ -376,11 +376,14 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
     return st;
 }
 
-// ---- autotuner: fused (16- or 8-row tiles) vs 3-pass, per workload ----------------
+// ---- autotuner: fused (plane-batched kernel, row-segment kernel with 16- or 8-row
+// tiles) vs 3-pass, per workload ---------------------------------------------------
+constexpr int kTuneCands = 4;
 struct TuneEntry {
     int form;
     int ty;
-    double ms[3];
+    int kernel;
+    double ms[kTuneCands];
 };
 // Probing in progress for a workload key: the next candidate, whether its warm-up step
 // has run, and the results so far.  Calls of a few steps each advance it in turn.
@@ -388,7 +391,7 @@ struct TuneProgress {
     int cand = 0;
     bool warmed = false;
     double best = 1e300;
-    TuneEntry entry{VL_FORM_FUSED, 0, {0.0, 0.0, 0.0}};
+    TuneEntry entry{VL_FORM_FUSED, 0, 0, {0.0, 0.0, 0.0, 0.0}};
 };
 std::mutex g_tune_mu;
 std::map<uint64_t, TuneEntry> g_tune;
@@ -425,8 +428,10 @@ void tune_load_locked()
     while (std::fgets(line, sizeof(line), f)) {
         unsigned long long key;
         TuneEntry e;
-        if (std::sscanf(line, "{\"key\": %llu, \"form\": %d, \"tile_rows\": %d, \"ms\": [%lf, %lf, %lf]}", &key,
-                        &e.form, &e.ty, &e.ms[0], &e.ms[1], &e.ms[2]) == 6)
+        if (std::sscanf(line,
+                        "{\"key\": %llu, \"form\": %d, \"tile_rows\": %d, \"kernel\": %d, "
+                        "\"ms\": [%lf, %lf, %lf, %lf]}",
+                        &key, &e.form, &e.ty, &e.kernel, &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3]) == 8)
             g_tune[(uint64_t)key] = e;
     }
     std::fclose(f);
@@ -439,8 +444,10 @@ void tune_store_locked(uint64_t key, const TuneEntry& e)
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": %llu, \"form\": %d, \"tile_rows\": %d, \"ms\": [%.6f, %.6f, %.6f]}\n",
-                 (unsigned long long)key, e.form, e.ty, e.ms[0], e.ms[1], e.ms[2]);
+    std::fprintf(f,
+                 "{\"key\": %llu, \"form\": %d, \"tile_rows\": %d, \"kernel\": %d, "
+                 "\"ms\": [%.6f, %.6f, %.6f, %.6f]}\n",
+                 (unsigned long long)key, e.form, e.ty, e.kernel, e.ms[0], e.ms[1], e.ms[2], e.ms[3]);
     std::fclose(f);
 }
 
@@ -853,6 +860,12 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
     a.tile[0] = opts.tile[0];
     a.tile[1] = opts.tile[1];
     a.ghost = opts.ghost;
+    if (opts.kernel < 0 || opts.kernel > 2) return fail(g, VL_EINVAL, "vl_translate: unknown fused kernel");
+    a.kernel = opts.kernel;
+    if (opts.kernel == 1 && opts.form != VL_FORM_3PASS && !gt3_applies(g, a))
+        return fail(g, VL_EINVAL,
+                    "vl_translate: the plane-batched kernel needs FP32 storage, GT3, a streamed axis y or z "
+                    "and no velocity block straddling v_d = 0");
     if (!g->ev_sweep0) {
         cudaEventCreate(&g->ev_sweep0);
         cudaEventCreate(&g->ev_sweep1);
@@ -867,7 +880,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
         // Section 3's trade-off measured on this workload: each candidate advances the
         // real state (they all compute the same step), one warm-up and one timed step.
         const uint64_t key = tune_key(g, a);
-        TuneEntry entry{VL_FORM_FUSED, 0, {0.0, 0.0, 0.0}};
+        TuneEntry entry{VL_FORM_FUSED, 0, 0, {0.0, 0.0, 0.0, 0.0}};
         bool known;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -877,8 +890,9 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
             if (known) entry = it->second;
         }
         if (!known) {
-            const int cand_form[3] = {VL_FORM_FUSED, VL_FORM_FUSED, VL_FORM_3PASS};
-            const int cand_ty[3] = {16, 8, 0};
+            const int cand_form[kTuneCands] = {VL_FORM_FUSED, VL_FORM_FUSED, VL_FORM_FUSED, VL_FORM_3PASS};
+            const int cand_ty[kTuneCands] = {16, 16, 8, 0};
+            const int cand_kernel[kTuneCands] = {1, 2, 2, 0};
             TuneProgress pr;
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -886,17 +900,21 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
             }
             // each candidate: one warm-up step, then one timed step, possibly over
             // several calls; every step advances the real state
-            while (st == VL_OK && pr.cand < 3 && done < nsteps) {
+            while (st == VL_OK && pr.cand < kTuneCands && done < nsteps) {
                 const int c = pr.cand;
-                // 16-row tiles need a z-last order; with 16-bit storage the 3-pass form
-                // rounds to storage after every sweep, so it is not the same computation
-                // as the fused form and only tile sizes are tuned
-                if ((cand_ty[c] == 16 && a.order[2] != 2) || (cand_form[c] == VL_FORM_3PASS && g->codec != 0)) {
+                // the plane-batched kernel where it applies; 16-row tiles of the
+                // row-segment kernel need a z-last order; with 16-bit storage the 3-pass
+                // form rounds to storage after every sweep, so it is not the same
+                // computation as the fused form and only the fused kernels are tuned
+                StepArgs ac = a;
+                ac.tile[1] = cand_ty[c];
+                ac.kernel = cand_kernel[c];
+                if ((cand_kernel[c] == 1 && !gt3_applies(g, ac)) ||
+                    (cand_kernel[c] == 2 && cand_ty[c] == 16 && a.order[2] != 2) ||
+                    (cand_form[c] == VL_FORM_3PASS && g->codec != 0)) {
                     pr.cand++;
                     continue;
                 }
-                StepArgs ac = a;
-                ac.tile[1] = cand_ty[c];
                 vl_step_stats probe{};
                 st = translate_steps(g, ac, cand_form[c] == VL_FORM_FUSED, 1, &probe);
                 if (st != VL_OK) break;
@@ -915,6 +933,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                 done += 1;
                 form = cand_form[c];
                 a.tile[1] = cand_ty[c];
+                a.kernel = cand_kernel[c];
                 if (!pr.warmed) {
                     pr.warmed = true;
                     continue;
@@ -924,25 +943,28 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                     pr.best = probe.device_ms;
                     pr.entry.form = cand_form[c];
                     pr.entry.ty = cand_ty[c];
+                    pr.entry.kernel = cand_kernel[c];
                 }
                 pr.cand++;
                 pr.warmed = false;
             }
             entry = pr.entry;
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            if (st == VL_OK && pr.cand >= 3) {
+            if (st == VL_OK && pr.cand >= kTuneCands) {
                 tune_store_locked(key, entry);
                 g_tune_progress.erase(key);
                 form = entry.form;
                 a.tile[1] = entry.ty;
+                a.kernel = entry.kernel;
             } else {
                 g_tune_progress[key] = pr;
             }
         } else {
             form = entry.form;
             a.tile[1] = entry.ty;
+            a.kernel = entry.kernel;
         }
-        for (int c = 0; c < 3; c++) S.tune_ms[c] = entry.ms[c];
+        for (int c = 0; c < kTuneCands; c++) S.tune_ms[c] = entry.ms[c];
         if (form == VL_FORM_AUTO) form = entry.form;  // no step ran in this call
     }
     const bool fused = form != VL_FORM_3PASS;
@@ -950,7 +972,8 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
         st = opts.graph ? translate_graph(g, a, fused, nsteps - done, opts.capacity, &S)
                         : translate_steps(g, a, fused, nsteps - done, &S);
     S.form_used = form;
-    S.tile_rows_used = fused ? tile_rows(a) : 0;
+    S.kernel_used = fused ? (use_gt3(g, a) ? 1 : 2) : 0;
+    S.tile_rows_used = fused ? (S.kernel_used == 1 ? 16 : tile_rows(a)) : 0;
     S.launches = launch_count() - launches0;
     if (S.steps > 0) g->stats = S;
     else g->stats.steps = 0;

@@ -624,14 +624,6 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 }
 
 // ---- work list ------------------------------------------------------------------
-struct TileArgs {
-    GridGeom G;
-    const uint64_t* ubits;
-    int ax[3];
-    int ntile0, ntile1;
-    int ty;
-};
-
 __device__ bool row_any(const uint64_t* rowp, int xlo, int xhi)
 {
     uint64_t acc = 0;
@@ -706,6 +698,19 @@ vl_status launch_fused(Grid* g, const FusedArgs& P)
 
 }  // namespace
 
+// Work list of a fused launch: one item per (block id, tile column) holding any slot of
+// the next layout, grouped by block id (item_base[b] .. item_base[b+1]).
+void launch_tile_list(Grid* g, const TileArgs& T, int64_t need, int64_t ntiles)
+{
+    k_tile_flags<<<nblk(need, 256), 256, 0, g->stream>>>(T, g->tile_flags);
+    note_launch();
+    launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, T.G.nb, g->stream, T.G.abort);
+    launch_base_scan(g->item_cnt, g->item_base, T.G.nb, g->stream, T.G.abort);
+    k_tile_items<<<nblk(need, 256), 256, 0, g->stream>>>(ntiles, T.G.nb, g->tile_flags, g->tile_pos,
+                                                           g->item_base, g->items, T.G.abort);
+    note_launch();
+}
+
 // Work-list buffers of the fused form for this sweep order (allocated before any
 // captured step sequence).
 // Tile rows along the second sweep axis: 16 when the streamed axis is the velocity
@@ -735,6 +740,7 @@ vl_status fused_worklist_alloc(Grid* g, const StepArgs& a)
 
 vl_status run_fused(Grid* g, const StepArgs& a)
 {
+    if (use_gt3(g, a)) return run_gt3(g, a);
     const GridGeom& G = g->geom;
     Layout& A = g->lay[g->cur];
     Layout& B = g->lay[1 - g->cur];
@@ -755,13 +761,7 @@ vl_status run_fused(Grid* g, const StepArgs& a)
     T.ntile0 = ntile0;
     T.ntile1 = ntile1;
     T.ty = ty;
-    k_tile_flags<<<nblk(need, 256), 256, 0, g->stream>>>(T, g->tile_flags);
-    note_launch();
-    launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, G.nb, g->stream, G.abort);
-    launch_base_scan(g->item_cnt, g->item_base, G.nb, g->stream, G.abort);
-    k_tile_items<<<nblk(need, 256), 256, 0, g->stream>>>(ntiles, G.nb, g->tile_flags, g->tile_pos,
-                                                           g->item_base, g->items, G.abort);
-    note_launch();
+    launch_tile_list(g, T, need, ntiles);
 
     FusedArgs P;
     P.G = G;

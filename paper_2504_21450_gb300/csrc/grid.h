@@ -153,6 +153,9 @@ struct StepArgs {
     StepCounters* ctr;    // counters of this step
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the sweep kernels when set
     bool stamp_ctas = false;  // fused kernel: each CTA records when it ran out of work
+    int kernel = 0;       // fused form: 0 plane-batched where it applies and no row-segment
+                          // tile is asked for (tile[1]), else row-segment; 1 plane-batched
+                          // (VL_EINVAL where it does not apply); 2 row-segment
     bool ev_node = false;  // inside a stream capture: record as event record nodes
 };
 // Host-side fault injection for tests: true when the environment variable VLGT_FAULT
@@ -189,6 +192,24 @@ inline void record_sweep_event(cudaEvent_t ev, cudaStream_t s, bool node)
     else cudaEventRecord(ev, s);
 }
 constexpr int kMaxCtas = 4096;  // CTAs of a persistent fused launch, at most
+// Tiles of a fused launch: TX (16) cells along axis ax[0], ty along ax[1], ax[2] whole.
+struct TileArgs {
+    GridGeom G;
+    const uint64_t* ubits;
+    int ax[3];
+    int ntile0, ntile1;
+    int ty;
+};
+void launch_tile_list(Grid* g, const TileArgs& T, int64_t need, int64_t ntiles);
+// gt3.cu: the plane-batched GT3 kernel (FP32 storage, GT3, streamed axis y or z, no
+// velocity block straddling v_d = 0)
+bool gt3_applies(const Grid* g, const StepArgs& a);
+vl_status run_gt3(Grid* g, const StepArgs& a);
+inline bool use_gt3(const Grid* g, const StepArgs& a)
+{
+    if (a.kernel == 2 || (a.kernel == 0 && a.tile[1] != 0)) return false;  // row-segment tiles asked for
+    return gt3_applies(g, a);
+}
 vl_status fused_worklist_alloc(Grid* g, const StepArgs& a);
 int tile_rows(const StepArgs& a);
 vl_status run_fused(Grid* g, const StepArgs& a);

@@ -42,7 +42,7 @@ class vl_device(ctypes.Structure):
 class vl_translate_opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("limiter", ctypes.c_int), ("ghost", ctypes.c_int),
                 ("tile", ctypes.c_int * 2), ("check", ctypes.c_int), ("graph", ctypes.c_int),
-                ("reserved0", ctypes.c_int), ("capacity", ctypes.c_int64), ("reserved", ctypes.c_int * 4)]
+                ("kernel", ctypes.c_int), ("capacity", ctypes.c_int64), ("reserved", ctypes.c_int * 4)]
 
 
 class vl_step_stats(ctypes.Structure):
@@ -54,8 +54,9 @@ class vl_step_stats(ctypes.Structure):
                 ("prune_ms", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("graph_replays", ctypes.c_int64), ("capacity_regrows", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("form_used", ctypes.c_int),
-                ("tile_rows_used", ctypes.c_int), ("tune_ms", ctypes.c_double * 3),
-                ("updates", ctypes.c_int64), ("tail_ms", ctypes.c_double)]
+                ("tile_rows_used", ctypes.c_int), ("tune_ms", ctypes.c_double * 4),
+                ("updates", ctypes.c_int64), ("tail_ms", ctypes.c_double),
+                ("kernel_used", ctypes.c_int), ("reserved_stats", ctypes.c_int)]
 
 
 class VlError(RuntimeError):
@@ -368,9 +369,10 @@ class Grid:
 
     def translate(self, dt: float, order: str = "xyz", nsteps: int = 1, form: int = VL_FORM_FUSED,
                   limiter: bool = True, check: bool = False, graph: bool = False, capacity: int = 0,
-                  tile_rows: int = 0, ghost: int = 3):
+                  tile_rows: int = 0, ghost: int = 3, kernel: int = 0):
         o = vl_translate_opts_default()
         o.tile[1] = int(tile_rows)
+        o.kernel = int(kernel)
         o.ghost = int(ghost)
         o.form = int(form)
         o.limiter = int(bool(limiter))

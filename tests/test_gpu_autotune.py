@@ -1,6 +1,7 @@
-"""The form/tile autotuner: probes the fused Ghost Translation kernel with 16- and 8-row
-tiles and the classical 3-pass form on the first steps of a workload (Section 3's
-trade-off measured per workload) and keeps the fastest."""
+"""The form/kernel autotuner: probes the fused Ghost Translation form (the plane-batched
+kernel where it applies, the row-segment kernel with 16- and 8-row tiles) and the
+classical 3-pass form on the first steps of a workload (Section 3's trade-off measured
+per workload) and keeps the fastest."""
 import json
 import os
 import subprocess
@@ -59,9 +60,11 @@ def test_autotuned_run_equals_fixed_form():
         np.testing.assert_array_equal(x, y)
     assert s.steps == 8
     assert s.form_used in (vlasov.VL_FORM_FUSED, vlasov.VL_FORM_3PASS)
-    assert all(t > 0 for t in s.tune_ms)  # all three candidates probed (order ends in z)
-    best = int(np.argmin(list(s.tune_ms)))
-    assert s.form_used == (vlasov.VL_FORM_3PASS if best == 2 else vlasov.VL_FORM_FUSED)
+    # the velocity mesh has blocks straddling v_y = 0: no plane-batched candidate; the
+    # other three are probed (order ends in z)
+    assert s.tune_ms[0] == 0 and all(t > 0 for t in s.tune_ms[1:])
+    best = 1 + int(np.argmin(list(s.tune_ms[1:])))
+    assert s.form_used == (vlasov.VL_FORM_3PASS if best == 3 else vlasov.VL_FORM_FUSED)
 
 
 def test_tuning_cache_persists(tmp_path):
@@ -77,7 +80,7 @@ def test_tuning_cache_persists(tmp_path):
     first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert first.returncode == 0, first.stderr
     rec = [json.loads(line) for line in cache.read_text().splitlines()]
-    assert len(rec) == 1 and rec[0]["form"] in (0, 1) and len(rec[0]["ms"]) == 3
+    assert len(rec) == 1 and rec[0]["form"] in (0, 1) and len(rec[0]["ms"]) == 4
     second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert second.returncode == 0, second.stderr
     assert len(cache.read_text().splitlines()) == 1  # reused, not re-tuned
@@ -100,9 +103,26 @@ def test_probing_advances_over_single_step_calls():
         s = g.stats()
         forms.append(s.form_used)
     assert forms[:6] == [vlasov.VL_FORM_FUSED] * 4 + [vlasov.VL_FORM_3PASS] * 2  # the probes
-    assert all(t > 0 for t in s.tune_ms)
-    best = int(np.argmin(list(s.tune_ms)))
-    assert forms[6] == forms[7] == (vlasov.VL_FORM_3PASS if best == 2 else vlasov.VL_FORM_FUSED)
+    assert s.tune_ms[0] == 0 and all(t > 0 for t in s.tune_ms[1:])
+    best = 1 + int(np.argmin(list(s.tune_ms[1:])))
+    assert forms[6] == forms[7] == (vlasov.VL_FORM_3PASS if best == 3 else vlasov.VL_FORM_FUSED)
     for x, y in zip(ref, g.get_blocks()):
         np.testing.assert_array_equal(x, y)
     g.close()
+
+
+def test_plane_batched_kernel_is_probed_where_it_applies():
+    """A velocity mesh with no block straddling v = 0: all four candidates are timed,
+    the fastest is used, and the state equals a fixed-form run's."""
+    n = (40, 33, 18)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.3, seed=72)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    ref, _ = run(mesh, init, 10, vlasov.VL_FORM_3PASS)
+    got, s = run(mesh, init, 10, vlasov.VL_FORM_AUTO)
+    for x, y in zip(ref, got):
+        np.testing.assert_array_equal(x, y)
+    assert all(t > 0 for t in s.tune_ms)
+    best = int(np.argmin(list(s.tune_ms)))
+    assert s.form_used == (vlasov.VL_FORM_3PASS if best == 3 else vlasov.VL_FORM_FUSED)
+    if best < 3:
+        assert s.kernel_used == (1 if best == 0 else 2)

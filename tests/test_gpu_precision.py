@@ -129,7 +129,7 @@ def test_auto_form_with_16bit_storage_tunes_tiles_only():
     g.set_blocks(off, ids, vals)
     g.translate(0.2, "xyz", 6, vlasov.VL_FORM_AUTO, check=True)
     s = g.stats()
-    assert s.form_used == vlasov.VL_FORM_FUSED and s.tune_ms[2] == 0.0
+    assert s.form_used == vlasov.VL_FORM_FUSED and s.tune_ms[3] == 0.0
     g.close()
 
 
