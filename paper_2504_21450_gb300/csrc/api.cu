@@ -408,6 +408,9 @@ uint64_t tune_key(const Grid* g, const StepArgs& a)
     }
     k = mix(k, (uint64_t)a.limiter);
     k = mix(k, (uint64_t)g->codec);
+    // the candidates differ where the plane-batched kernel does not apply (velocity
+    // blocks straddling v = 0, an x-last order)
+    k = mix(k, (uint64_t)gt3_applies(g, a));
     // sparsity class: slots per cell rounded to a power of two
     const int64_t t = std::max<int64_t>(g->lay[g->cur].total, 1);
     int lg = 0;

@@ -51,11 +51,13 @@ struct Gt3Smem {
     float buf[2][kNB][kPS];   // staged planes, swept in place (two batches in flight)
     int orank[2][kNB][kT * kT];  // sparse output slots of the tile cells, per plane
     float4 kc[3][kChunk];     // WalkConst (g, A, B, up) per sweep and velocity cell
-    int run[kE][3];           // contiguous runs of a staged row along x: u0, x, len
-    int rrow[kE];             // row-space part of each staged row's in-plane coordinate
+    int run[2][kE][3];        // per item parity: contiguous runs of a staged row along x
+    int rrow[2][kE];          // per item parity: row-space part of each staged row
     uint64_t bar[2];          // staging barriers, one per batch buffer
-    long long work;
-    int nrun;
+    long long work;           // the current work item
+    long long next;           // the one after it (taken while the current one runs)
+    int nrun[2];
+    int pref;                 // batch 0 of the current item was staged during the last one
     int abort;
 };
 constexpr size_t kSmem = sizeof(Gt3Smem);
@@ -156,6 +158,172 @@ __device__ __forceinline__ void sts2(float* p, float2 v) { *reinterpret_cast<flo
 // row-space contribution (row = y + ny*z) of coordinate c along physical axis d (1 or 2)
 __device__ __forceinline__ int rowpart(int d, int c, int ny) { return d == 1 ? c : c * ny; }
 
+// One work item: block id b, velocity chunk q, tile origin and extent.
+struct Item {
+    int b, q, tx0, tr0, ex, er;
+    bool dense_in, dense_out, up2;
+    int64_t ibase, obase;
+};
+
+__device__ __forceinline__ Item decode_item(const Gt3Args& P, int64_t w)
+{
+    const GridGeom& G = P.G;
+    int lo = 0, hb = G.nb;  // items are grouped by b, q-major then tile
+    while (hb - lo > 1) {
+        const int mid = (lo + hb) >> 1;
+        if (4 * P.item_base[mid] <= w) lo = mid;
+        else hb = mid;
+    }
+    Item it;
+    it.b = lo;
+    const int64_t mb = P.item_base[lo + 1] - P.item_base[lo];
+    const int64_t wl = w - 4 * P.item_base[lo];
+    it.q = (int)(wl / mb);
+    const uint32_t tile = P.items[P.item_base[lo] + (wl % mb)];
+    it.tx0 = (int)(tile % P.ntile0) * kT;
+    it.tr0 = (int)(tile / P.ntile0) * kT;
+    it.ex = min(kT, G.n[0] - it.tx0);
+    it.er = min(kT, G.n[P.ar] - it.tr0);
+    it.dense_in = (P.in.dense[lo] & 3) == 3;
+    it.dense_out = (P.out.dense[lo] & 1) != 0;
+    it.ibase = ((int64_t)P.in.base[lo] * 4 + (int64_t)it.q * P.in.cnt[lo]) * kChunk;
+    it.obase = ((int64_t)P.out.base[lo] * 4 + (int64_t)it.q * P.out.cnt[lo]) * kChunk;
+    // direction along the streamed axis (not x: the same for every velocity cell of the
+    // item, the host checks that no block straddles v = 0)
+    const int d = P.ax[2];
+    const int bc = d == 1 ? (lo / G.nbx) % G.nby : lo / (G.nbx * G.nby);
+    it.up2 = P.walk[d * P.nvmax + bc * 4 + (d == 2 ? it.q : 0)].w != 0.0f;
+    return it;
+}
+
+// Runs and row parts of an item's staged rows into table t (threads kNC-1-kE .. kNC-1).
+__device__ __forceinline__ void item_tables(const Gt3Args& P, Gt3Smem& S, const Item& it, int t, int tid)
+{
+    const int nx = P.G.n[0], nr = P.G.n[P.ar];
+    if (tid == kNC - 1) {
+        int u0 = 0, nrun = 0;
+        while (u0 < kE) {
+            const int x = wrapi(it.tx0 - kHalo + u0, nx);
+            const int len = min(kE - u0, nx - x);
+            S.run[t][nrun][0] = u0;
+            S.run[t][nrun][1] = x;
+            S.run[t][nrun][2] = len;
+            nrun++;
+            u0 += len;
+        }
+        S.nrun[t] = nrun;
+    } else if (tid >= kNC - 1 - kE && tid < kNC - 1) {
+        const int u = tid - (kNC - 1 - kE);
+        S.rrow[t][u] = rowpart(P.ar, wrapi(it.tr0 - kHalo + u, nr), P.G.n[1]);
+    }
+}
+
+// Staging of batch k of an item (planes kNB k .. kNB k + 2 of its stream) into buffer
+// g & 1, g = the CTA's running batch index; run by the kNS staging threads (sl = 0..127).
+__device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const Item& it, int t, int k,
+                                            unsigned g, int sl)
+{
+    const GridGeom& G = P.G;
+    const int nx = G.n[0], ny = G.n[1], a2 = P.ax[2], n2 = G.n[a2];
+    const int nsteps = n2 + kFirst;
+    const unsigned slot = g & 1u;
+    uint64_t* bar = &S.bar[slot];
+    const int nj = min(kNB, nsteps - kNB * k);
+    const int nrun = S.nrun[t];
+    const float* ipool = static_cast<const float*>(P.in.pool);
+    auto plane_of = [&](int s) { return it.up2 ? s - kHalo : n2 + 2 - s; };
+    auto out_of = [&](int s) { return it.up2 ? s - kFirst : n2 + 4 - s; };
+    if (it.dense_in) {
+        // one arrival carrying the batch's bytes; the copies of the other staging
+        // threads may complete before or after it
+        if (sl == 0) bar_arrive_tx(bar, (unsigned)(nj * kE * kE * kChunk * sizeof(float)));
+        if (sl < nj * kE) {
+            const int j = sl / kE, rho = sl - j * kE;
+            const int pz = wrapi(plane_of(kNB * k + j), n2);
+            const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
+            const float* src = ipool + it.ibase + row * nx * kChunk;
+            float* dst = &S.buf[slot][j][rho * kRP];
+            fence_async_smem();
+            for (int k2 = 0; k2 < nrun; k2++)
+                copy_g2s(dst + S.run[t][k2][0] * kChunk, src + S.run[t][k2][1] * kChunk,
+                         (unsigned)(S.run[t][k2][2] * kChunk * sizeof(float)), bar);
+        }
+    } else {
+        // runs of present cells (consecutive slots) as bulk copies, each announced to the
+        // barrier before it is issued; absent cells are zeroed.  The one arrival comes
+        // after every staging thread has announced its bytes.
+        if (sl < nj * kE) {
+            const int j = sl / kE, rho = sl - j * kE;
+            const int pz = wrapi(plane_of(kNB * k + j), n2);
+            const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
+            const int64_t wbase = (int64_t)it.b * G.RW + row * G.W;
+            float* dst = &S.buf[slot][j][rho * kRP];
+            fence_async_smem();
+            for (int k2 = 0; k2 < nrun; k2++) {
+                const int u0 = S.run[t][k2][0], x0 = S.run[t][k2][1], len = S.run[t][k2][2];
+                const int w0 = x0 >> 6, sh = x0 & 63;
+                const bool two = sh + len > 64;
+                const uint64_t ua = P.in.ubits[wbase + w0];
+                const uint64_t ub = two ? P.in.ubits[wbase + w0 + 1] : 0ull;
+                const uint32_t oa = P.in.woff[wbase + w0];
+                const uint32_t ob = two ? P.in.woff[wbase + w0 + 1] : 0u;
+                const uint64_t lenmask = (1ull << len) - 1ull;  // len <= 22
+                uint64_t pm = (P.in.kbits[wbase + w0] & ua) >> sh;
+                if (two) pm |= (P.in.kbits[wbase + w0 + 1] & ub) << (64 - sh);
+                pm &= lenmask;
+                uint64_t absent = ~pm & lenmask;
+                while (absent) {
+                    const int u = __ffsll((long long)absent) - 1;
+                    absent &= absent - 1ull;
+                    float4* z = reinterpret_cast<float4*>(dst + (u0 + u) * kChunk);
+                    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+                    z[0] = zero;
+                    z[1] = zero;
+                    z[2] = zero;
+                    z[3] = zero;
+                }
+                uint64_t m = pm;
+                while (m) {
+                    const int u = __ffsll((long long)m) - 1;
+                    const int rl = __ffsll((long long)~(m >> u)) - 1;
+                    const int x = x0 + u;
+                    const bool lw = (x >> 6) == w0;
+                    const int64_t r = (int64_t)(lw ? oa : ob) + __popcll((lw ? ua : ub) & ((1ull << (x & 63)) - 1ull));
+                    const unsigned bytes = (unsigned)(rl * kChunk * sizeof(float));
+                    bar_add_tx(bar, bytes);
+                    copy_g2s(dst + (u0 + u) * kChunk, ipool + it.ibase + r * kChunk, bytes, bar);
+                    m &= ~(((1ull << rl) - 1ull) << u);
+                }
+            }
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kNS) : "memory");
+        if (sl == 0) bar_arrive(bar);
+    }
+    // output slots of the tile cells of a sparse next layout
+    if (!it.dense_out && sl < nj * kT) {
+        const int j = sl / kT, rr = sl - j * kT;
+        const int s = kNB * k + j;
+        if (s >= kFirst) {
+            const int zo = out_of(s);
+            int* orow = &S.orank[slot][j][rr * kT];
+            uint64_t uw = 0ull;
+            uint32_t ow = 0u;
+            if (rr < it.er) {
+                const int64_t row = (int64_t)rowpart(P.ar, it.tr0 + rr, ny) + rowpart(a2, zo, ny);
+                const int64_t wi = (int64_t)it.b * G.RW + row * G.W + (it.tx0 >> 6);
+                uw = P.out.ubits[wi];
+                ow = P.out.woff[wi];
+            }
+#pragma unroll
+            for (int i = 0; i < kT; i++) {
+                const int bit = (it.tx0 + i) & 63;  // the 16 cells share one bitmap word
+                const bool has = i < it.ex && ((uw >> bit) & 1ull);
+                orow[i] = has ? (int)(ow + __popcll(uw & ((1ull << bit) - 1ull))) : -1;
+            }
+        }
+    }
+}
+
 template <bool kLim, bool kA0X>
 __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
 {
@@ -168,7 +336,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
     const bool stager = tid >= kNY;   // warps 12-15: stage the next batch during sweep 1
     const int sl = tid - kNY;         // staging lane 0..127
     const int ar = P.ar, a2 = P.ax[2];
-    const int nx = G.n[0], nr = G.n[ar], n2 = G.n[a2], ny = G.n[1];
+    const int n2 = G.n[a2];
     const int nsteps = n2 + kFirst;       // planes streamed per item (3 before, 2 after)
     const int nbatch = (nsteps + kNB - 1) / kNB;
     const int64_t nwork = 4 * P.item_base[G.nb];
@@ -182,174 +350,48 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
         bar_init(&S.bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         S.abort = 0;
+        S.pref = 0;
+        S.work = (long long)atomicAdd(&P.ctr->work_next, 1ull);
     }
-    unsigned gb = 0;  // batches staged by this CTA before the current item (barrier phases)
+    unsigned gb = 0;   // batches staged by this CTA before the current item (barrier phases)
+    unsigned ni = 0;   // items taken by this CTA (parity selects the run and row tables)
     float msum = 0.0f, mcomp = 0.0f;  // Kahan-compensated FP32 mass of this thread
 
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) S.work = (long long)atomicAdd(&P.ctr->work_next, 1ull);
+    for (;; ni++) {
         __syncthreads();
         const int64_t w = S.work;
         if (w >= nwork || S.abort) break;
-
-        // ---- decode (b, q, tile); items are grouped by b, q-major then tile --------
-        int lo = 0, hb = G.nb;
-        while (hb - lo > 1) {
-            const int mid = (lo + hb) >> 1;
-            if (4 * P.item_base[mid] <= w) lo = mid;
-            else hb = mid;
-        }
-        const int b = lo;
-        const int64_t mb = P.item_base[b + 1] - P.item_base[b];
-        const int64_t wl = w - 4 * P.item_base[b];
-        const int q = (int)(wl / mb);
-        const uint32_t tile = P.items[P.item_base[b] + (wl % mb)];
-        const int tx0 = (int)(tile % P.ntile0) * kT;  // tile origin along x
-        const int tr0 = (int)(tile / P.ntile0) * kT;  // and along the other in-plane axis
-        const int ex = min(kT, nx - tx0), er = min(kT, nr - tr0);
-        const bool dense_in = (P.in.dense[b] & 3) == 3;
-        const bool dense_out = (P.out.dense[b] & 1) != 0;
-        const int64_t ibase = ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk;
-        const int64_t obase = ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk;
-        const int64_t okeep = (int64_t)P.out.base[b];
-        const float* ipool = static_cast<const float*>(P.in.pool);
+        const bool pref = S.pref != 0;
+        const int ti = (int)(ni & 1u);
+        const Item it = decode_item(P, w);
+        const int64_t okeep = (int64_t)P.out.base[it.b];
         float* opool = static_cast<float*>(P.out.pool);
-
-        if (tid == kNC - 1) {
-            int u0 = 0, nrun = 0;
-            while (u0 < kE) {
-                const int x = wrapi(tx0 - kHalo + u0, nx);
-                const int len = min(kE - u0, nx - x);
-                S.run[nrun][0] = u0;
-                S.run[nrun][1] = x;
-                S.run[nrun][2] = len;
-                nrun++;
-                u0 += len;
-            }
-            S.nrun = nrun;
-        } else if (tid >= kNC - 1 - kE) {
-            const int u = tid - (kNC - 1 - kE);
-            S.rrow[u] = rowpart(ar, wrapi(tr0 - kHalo + u, nr), ny);
-        } else if (tid < 3 * kChunk) {
+        if (!pref) item_tables(P, S, it, ti, tid);
+        if (tid < 3 * kChunk) {
             // sweep constants of the item's 16 velocity cells (v = vx + 4 vy, vz = q)
             const int j = tid >> 4, l = tid & 15;
             const int d = P.ax[j];
-            const int bc = d == 0 ? b % G.nbx : (d == 1 ? (b / G.nbx) % G.nby : b / (G.nbx * G.nby));
-            const int wi = d == 0 ? (l & 3) : (d == 1 ? (l >> 2) : q);
+            const int bc = d == 0 ? it.b % G.nbx : (d == 1 ? (it.b / G.nbx) % G.nby : it.b / (G.nbx * G.nby));
+            const int wi = d == 0 ? (l & 3) : (d == 1 ? (l >> 2) : it.q);
             S.kc[j][l] = P.walk[d * P.nvmax + bc * 4 + wi];
+        } else if (tid == kNC - 2 - kE) {
+            S.next = (long long)atomicAdd(&P.ctr->work_next, 1ull);
         }
         __syncthreads();  // per-item tables ready
-        const bool up0 = S.kc[0][0].w != 0.0f, up1 = S.kc[1][0].w != 0.0f, up2 = S.kc[2][0].w != 0.0f;
-        // streamed plane of step s and the output plane it completes
-        auto plane_of = [&](int s) { return up2 ? s - kHalo : n2 + 2 - s; };
-        auto out_of = [&](int s) { return up2 ? s - kFirst : n2 + 4 - s; };
-
-        // ---- staging threads: batch k into buffer (gb + k) & 1 ----------------------
-        auto stage = [&](int k) {
-            const unsigned slot = (gb + k) & 1u;
-            uint64_t* bar = &S.bar[slot];
-            const int nj = min(kNB, nsteps - kNB * k);
-            const int nrun = S.nrun;
-            if (dense_in) {
-                // one arrival carrying the batch's bytes; the copies of the other
-                // staging threads may complete before or after it
-                if (sl == 0) bar_arrive_tx(bar, (unsigned)(nj * kE * kE * kChunk * sizeof(float)));
-                if (sl < nj * kE) {
-                    const int j = sl / kE, rho = sl - j * kE;
-                    const int pz = wrapi(plane_of(kNB * k + j), n2);
-                    const int64_t row = (int64_t)S.rrow[rho] + rowpart(a2, pz, ny);
-                    const float* src = ipool + ibase + row * nx * kChunk;
-                    float* dst = &S.buf[slot][j][rho * kRP];
-                    fence_async_smem();
-                    for (int k2 = 0; k2 < nrun; k2++)
-                        copy_g2s(dst + S.run[k2][0] * kChunk, src + S.run[k2][1] * kChunk,
-                                 (unsigned)(S.run[k2][2] * kChunk * sizeof(float)), bar);
-                }
-            } else {
-                // runs of present cells (consecutive slots) as bulk copies, each announced
-                // to the barrier before it is issued; absent cells are zeroed.  The one
-                // arrival comes after every staging thread has announced its bytes.
-                if (sl < nj * kE) {
-                    const int j = sl / kE, rho = sl - j * kE;
-                    const int pz = wrapi(plane_of(kNB * k + j), n2);
-                    const int64_t row = (int64_t)S.rrow[rho] + rowpart(a2, pz, ny);
-                    const int64_t wbase = (int64_t)b * G.RW + row * G.W;
-                    float* dst = &S.buf[slot][j][rho * kRP];
-                    fence_async_smem();
-                    for (int k2 = 0; k2 < nrun; k2++) {
-                        const int u0 = S.run[k2][0], x0 = S.run[k2][1], len = S.run[k2][2];
-                        const int w0 = x0 >> 6, sh = x0 & 63;
-                        const bool two = sh + len > 64;
-                        const uint64_t ua = P.in.ubits[wbase + w0];
-                        const uint64_t ub = two ? P.in.ubits[wbase + w0 + 1] : 0ull;
-                        const uint32_t oa = P.in.woff[wbase + w0];
-                        const uint32_t ob = two ? P.in.woff[wbase + w0 + 1] : 0u;
-                        const uint64_t lenmask = (1ull << len) - 1ull;  // len <= 22
-                        uint64_t pm = (P.in.kbits[wbase + w0] & ua) >> sh;
-                        if (two) pm |= (P.in.kbits[wbase + w0 + 1] & ub) << (64 - sh);
-                        pm &= lenmask;
-                        uint64_t absent = ~pm & lenmask;
-                        while (absent) {
-                            const int u = __ffsll((long long)absent) - 1;
-                            absent &= absent - 1ull;
-                            float4* z = reinterpret_cast<float4*>(dst + (u0 + u) * kChunk);
-                            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-                            z[0] = zero;
-                            z[1] = zero;
-                            z[2] = zero;
-                            z[3] = zero;
-                        }
-                        uint64_t m = pm;
-                        while (m) {
-                            const int u = __ffsll((long long)m) - 1;
-                            const int rl = __ffsll((long long)~(m >> u)) - 1;
-                            const int x = x0 + u;
-                            const bool lw = (x >> 6) == w0;
-                            const int64_t r = (int64_t)(lw ? oa : ob) +
-                                              __popcll((lw ? ua : ub) & ((1ull << (x & 63)) - 1ull));
-                            const unsigned bytes = (unsigned)(rl * kChunk * sizeof(float));
-                            bar_add_tx(bar, bytes);
-                            copy_g2s(dst + (u0 + u) * kChunk, ipool + ibase + r * kChunk, bytes, bar);
-                            m &= ~(((1ull << rl) - 1ull) << u);
-                        }
-                    }
-                }
-                asm volatile("bar.sync 1, %0;\n" ::"n"(kNS) : "memory");
-                if (sl == 0) bar_arrive(bar);
-            }
-            // output slots of the tile cells of a sparse next layout
-            if (!dense_out && sl < nj * kT) {
-                const int j = sl / kT, rr = sl - j * kT;
-                const int s = kNB * k + j;
-                if (s >= kFirst) {
-                    const int zo = out_of(s);
-                    int* orow = &S.orank[slot][j][rr * kT];
-                    uint64_t uw = 0ull;
-                    uint32_t ow = 0u;
-                    if (rr < er) {
-                        const int64_t row = (int64_t)rowpart(ar, tr0 + rr, ny) + rowpart(a2, zo, ny);
-                        const int64_t wi = (int64_t)b * G.RW + row * G.W + (tx0 >> 6);
-                        uw = P.out.ubits[wi];
-                        ow = P.out.woff[wi];
-                    }
-#pragma unroll
-                    for (int i = 0; i < kT; i++) {
-                        const int bit = (tx0 + i) & 63;  // the 16 cells share one bitmap word
-                        const bool has = i < ex && ((uw >> bit) & 1ull);
-                        orow[i] = has ? (int)(ow + __popcll(uw & ((1ull << bit) - 1ull))) : -1;
-                    }
-                }
-            }
-        };
+        if (tid == 0) {
+            S.pref = 0;
+            S.work = S.next;
+        }
+        const bool up0 = S.kc[0][0].w != 0.0f, up1 = S.kc[1][0].w != 0.0f;
+        auto out_of = [&](int s) { return it.up2 ? s - kFirst : n2 + 4 - s; };
 
         // ---- sweep-2 state of this thread: two tile cells, one vx row of the chunk ----
         const int zq = tid & 3;             // vy of the thread's vx row
         const int zc = tid >> 2;            // tile cells zc and zc + 128
         const int zcx = zc & 15, zcr = zc >> 4;
-        const bool zv0 = zcx < ex && zcr < er, zv1 = zcx < ex && zcr + 8 < er;
+        const bool zv0 = zcx < it.ex && zcr < it.er, zv1 = zcx < it.ex && zcr + 8 < it.er;
         const int zoff = (kHalo + zcr) * kRP + (kHalo + zcx) * kChunk + 4 * zq;
-        const int64_t zcell = (int64_t)(tx0 + zcx) + (int64_t)(tr0 + zcr) * str_r;  // at plane 0
+        const int64_t zcell = (int64_t)(it.tx0 + zcx) + (int64_t)(it.tr0 + zcr) * str_r;  // at plane 0
         Walk2<kLim> zw[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) zw[i].reset();
@@ -361,7 +403,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             kz.B = make_float2(c.z, c.z);
         }
 
-        if (stager) stage(0);
+        if (stager && !pref) stage_batch(P, S, it, ti, 0, gb, sl);
         int k = 0;
         for (; k < nbatch; k++) {
             const unsigned slot = (gb + k) & 1u;
@@ -401,7 +443,19 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             __syncthreads();  // sweep 0 complete; the buffer of batch k-1 is free
             if (S.abort) break;
             if (stager) {
-                if (k + 1 < nbatch) stage(k + 1);
+                if (k + 1 < nbatch) {
+                    stage_batch(P, S, it, ti, k + 1, gb + k + 1, sl);
+                } else {
+                    // last batch: stage the first batch of the next item
+                    const int64_t wn = S.next;
+                    if (wn < nwork) {
+                        const Item nx = decode_item(P, wn);
+                        item_tables(P, S, nx, ti ^ 1, tid);
+                        asm volatile("bar.sync 1, %0;\n" ::"n"(kNS) : "memory");
+                        stage_batch(P, S, nx, ti ^ 1, 0, gb + nbatch, sl);
+                        if (sl == 0) S.pref = 1;
+                    }
+                }
             } else {
                 // sweep 1 along axis 1 on the tile lines
                 const int j = tid >> 7, rem = tid & 127;
@@ -432,7 +486,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             fence_async_smem();
             __syncthreads();  // sweep 1 complete
             // sweep 2: push the batch's planes through the streamed windows and emit
-            for (int j = 0; j < nj; j++) {
+            auto zplane = [&](int j) {
                 const int s = kNB * k + j;
                 const float* src = B + j * kPS + zoff;
                 const float4 y0 = *reinterpret_cast<const float4*>(src);
@@ -441,10 +495,10 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                 const float2 r01 = zw[1].push(make_float2(y0.z, y0.w), kz);
                 const float2 r10 = zw[2].push(make_float2(y1.x, y1.y), kz);
                 const float2 r11 = zw[3].push(make_float2(y1.z, y1.w), kz);
-                if (s < kFirst) continue;
+                if (s < kFirst) return;
                 const int zo = out_of(s);
                 int64_t rk0, rk1;
-                if (dense_out) {
+                if (it.dense_out) {
                     const int64_t c = zcell + (int64_t)zo * str_2;
                     rk0 = zv0 ? c : -1;
                     rk1 = zv1 ? c + 8 * str_r : -1;
@@ -456,13 +510,13 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                 float psum = 0.0f;
                 bool keep0 = false, keep1 = false;
                 if (rk0 >= 0) {
-                    *reinterpret_cast<float4*>(opool + obase + rk0 * kChunk + 4 * zq) =
+                    *reinterpret_cast<float4*>(opool + it.obase + rk0 * kChunk + 4 * zq) =
                         make_float4(r00.x, r00.y, r01.x, r01.y);
                     psum += (r00.x + r00.y) + (r01.x + r01.y);
                     keep0 = fmaxf(fmaxf(r00.x, r00.y), fmaxf(r01.x, r01.y)) >= P.thr;
                 }
                 if (rk1 >= 0) {
-                    *reinterpret_cast<float4*>(opool + obase + rk1 * kChunk + 4 * zq) =
+                    *reinterpret_cast<float4*>(opool + it.obase + rk1 * kChunk + 4 * zq) =
                         make_float4(r10.x, r10.y, r11.x, r11.y);
                     psum += (r10.x + r10.y) + (r11.x + r11.y);
                     keep1 = fmaxf(fmaxf(r10.x, r10.y), fmaxf(r11.x, r11.y)) >= P.thr;
@@ -471,13 +525,19 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                 const unsigned b0 = __ballot_sync(0xffffffffu, keep0);
                 const unsigned b1 = __ballot_sync(0xffffffffu, keep1);
                 if (zq == 0) {
-                    if ((b0 >> (lane & ~3)) & 0xfu) P.keepq[(okeep + rk0) * 4 + q] = 1;
-                    if ((b1 >> (lane & ~3)) & 0xfu) P.keepq[(okeep + rk1) * 4 + q] = 1;
+                    if ((b0 >> (lane & ~3)) & 0xfu) P.keepq[(okeep + rk0) * 4 + it.q] = 1;
+                    if ((b1 >> (lane & ~3)) & 0xfu) P.keepq[(okeep + rk1) * 4 + it.q] = 1;
                 }
                 const float y = psum - mcomp;
                 const float t = msum + y;
                 mcomp = (t - msum) - y;
                 msum = t;
+            };
+            if (nj == kNB) {
+#pragma unroll
+                for (int j = 0; j < kNB; j++) zplane(j);
+            } else {
+                for (int j = 0; j < nj; j++) zplane(j);
             }
         }
         if (S.abort) {
