@@ -192,8 +192,11 @@ vl_status vl_grid_create(const vl_space_desc* space, const vl_vmesh_desc* vmesh,
 vl_status vl_grid_destroy(vl_grid* grid);
 
 /* Replace the grid's state by the given per-cell lists.  on_device = 0: host pointers
- * (copied synchronously); 1: device pointers on the grid's device (read on its stream
- * before the call returns).  nblocks = cell_offsets[ncells].  values are float32; with
+ * (copied synchronously; when `values` is page-locked host memory -- cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister -- the scatter kernel reads it in place, over
+ * NVLink-C2C on a Grace host, else it is staged through device buffers); 1: device
+ * pointers on the grid's device (read on its stream before the call returns).
+ * nblocks = cell_offsets[ncells].  values are float32; with
  * 16-bit storage they are rounded to it after the scale of each block id is taken from
  * their largest magnitude (host values then cross to the device twice).
  * Errors: VL_EINVAL (offsets not non-decreasing, ids out of range or not strictly
@@ -205,7 +208,8 @@ vl_status vl_set_blocks(vl_grid* grid, int64_t nblocks, const int64_t* cell_offs
 vl_status vl_get_block_count(vl_grid* grid, int64_t* nblocks);
 
 /* Copy the state out as per-cell lists into caller-allocated buffers of at least
- * `capacity` blocks (cell_offsets: ncells+1 entries).  on_device as in vl_set_blocks.
+ * `capacity` blocks (cell_offsets: ncells+1 entries).  on_device as in vl_set_blocks
+ * (page-locked host `values` are written in place by the gather kernel).
  * Errors: VL_ECAPACITY when capacity < vl_get_block_count. */
 vl_status vl_get_blocks(vl_grid* grid, int64_t capacity, int64_t* cell_offsets,
                         uint16_t* block_ids, float* values, int on_device);

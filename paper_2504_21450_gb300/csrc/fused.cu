@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
     __shared__ __align__(8) uint64_t s_bar[NST];  // staging barriers of the bulk copies
     __shared__ int s_run[EX][3];                  // contiguous runs of a halo row: u0, x, len
     __shared__ int s_nrun;
+    __shared__ int s_abort[2];  // a staging wait of an even / odd plane ran out: stop and leave
 
     const GridGeom& G = P.G;
     if (aborted(G.abort)) return;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
     if (tid == 0) {
         for (int k = 0; k < NST; k++) mbar_init(&s_bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort[0] = s_abort[1] = 0;
     }
     unsigned gstep = 0;  // planes staged by this CTA so far (barrier phases)
 
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         if (tid == 0) s_work = (int64_t)atomicAdd(&P.ctr->work_next, 1ull);
         __syncthreads();
         const int64_t w = s_work;
-        if (w >= nwork) break;
+        if (w >= nwork || s_abort[0] || s_abort[1]) break;
 
         // ---- decode (b, q, tile); items are grouped by b, q-major then tile --------
         int lo = 0, hb = G.nb;
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 while (!mbar_try_wait(bar, parity)) {
                     if (++polls > kMaxPolls || ((polls & 63u) == 0 && globaltimer_ns() - t0 > kWaitNs)) {
                         atomicOr(&P.ctr->error, 4);
+                        s_abort[s & 1] = 1;  // the CTA stops after this plane's barrier
                         break;
                     }
                 }
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         }
 
         // one streamed plane; kEmit: the plane completes an output plane
-        auto step = [&](int s, auto emit_tag) {
+        auto step = [&](int s, auto emit_tag) -> bool {
             constexpr bool kEmit = decltype(emit_tag)::value;
             wait_plane(s);
             // Bulk-staged planes: each thread's barrier wait makes plane s visible to it,
@@ -515,6 +518,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 issue_plane(s + NST - 1);
             }
             __syncthreads();  // sweep-0 rows complete
+            // a staging wait of this plane ran out: no sweep on an incomplete plane.  The
+            // flag is per plane parity, so no thread's wait on plane s+1 can change what
+            // the others read here.
+            if (s_abort[s & 1]) return true;
             // sweep 1 along axis 1 over rows j0..j0+L-1 of tile column ci, each output
             // pushed straight into the streamed window of its cell (sweep 2)
             const int zo = out_of(s);
@@ -600,10 +607,32 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 mcomp = (t - msum) - y;
                 msum = t;
             }
+            return false;
         };
         int s = 0;
-        for (; s < FIRST; s++) step(s, std::false_type{});
-        for (; s < nsteps; s++) step(s, std::true_type{});
+        bool stop = false;
+        for (; s < FIRST && !stop; s++) stop = step(s, std::false_type{});
+        for (; s < nsteps && !stop; s++) stop = step(s, std::true_type{});
+        if (stop) {
+            s--;  // the plane whose wait ran out
+            // leave no copy in flight: plane s ran out, planes s+1 .. s+NST-1 may have been
+            // issued; wait (bounded) for each before the CTA exits
+            if (bulk || sbulk) {
+                if (ltid == 0)
+                    for (int p = s; p < min(s + NST, nsteps); p++) {
+                        uint64_t* bar = &s_bar[(gstep + p) % NST];
+                        const unsigned parity = ((gstep + p) / NST) & 1u;
+                        unsigned polls = 0;
+                        const uint64_t t0 = globaltimer_ns();
+                        while (!mbar_try_wait(bar, parity) && ++polls <= kMaxPolls &&
+                               ((polls & 63u) != 0 || globaltimer_ns() - t0 <= kWaitNs)) {
+                        }
+                    }
+            } else {
+                cp_async_wait<0>();
+            }
+            break;
+        }
 
         __syncthreads();
         if (loader) {

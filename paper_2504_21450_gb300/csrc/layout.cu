@@ -725,6 +725,19 @@ struct Scratch {
 };
 }  // namespace
 
+// Device address of a page-locked host buffer (cudaHostAlloc, cudaMallocHost or
+// cudaHostRegister), through which kernels read and write it directly -- over
+// NVLink-C2C on a Grace host -- or nullptr for any other pointer.
+static void* mapped_host(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* ids_in,
                      const float* vals_in, int on_device, const float* scale_host,
                      const unsigned* vmax_host)
@@ -736,7 +749,10 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     Scratch sc(g);
     const int64_t* off = off_in;
     const uint16_t* ids = ids_in;
-    const float* vals = on_device ? vals_in : nullptr;  // host values are streamed below
+    // host values: read in place by the scatter kernel when the buffer is page-locked,
+    // else streamed through device staging buffers below
+    const float* mapped = (!on_device && M > 0) ? static_cast<const float*>(mapped_host(vals_in)) : nullptr;
+    const float* vals = on_device ? vals_in : mapped;
     if (!on_device) {
         int64_t* d_off = (int64_t*)sc.get((size_t)(G.N + 1) * 8);
         uint16_t* d_ids = (uint16_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 2);
@@ -788,7 +804,8 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     // kernel that consumes the previous one
     float* stage_buf[2] = {nullptr, nullptr};
     cudaEvent_t ready = nullptr, copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
-    const bool staged = M > 0 && !on_device;
+    const bool staged = M > 0 && !on_device && !mapped;
+    const bool direct = on_device || mapped;  // the kernels read vals in place
     const int npass = (g->codec && !given) ? 2 : 1;
     // two buffers when more than one chunk goes through them (over both passes)
     const int nbuf = (npass * ((M + chunk - 1) / chunk) > 1) ? 2 : 1;
@@ -811,10 +828,10 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     }
     int64_t k = 0;  // chunk counter over both passes (staging buffer k % nbuf)
     for (int pass = (g->codec && !given ? 0 : 1); pass < 2 && M > 0; pass++) {
-        for (int64_t t0 = 0; t0 < M; t0 += (on_device ? M : chunk), k++) {
-            const int64_t m = on_device ? M : std::min(chunk, M - t0);
+        for (int64_t t0 = 0; t0 < M; t0 += (direct ? M : chunk), k++) {
+            const int64_t m = direct ? M : std::min(chunk, M - t0);
             const int bi = (int)(k % nbuf);
-            const float* v = on_device ? vals : stage_buf[bi];
+            const float* v = direct ? vals : stage_buf[bi];
             if (staged) {
                 if (k >= nbuf) cudaStreamWaitEvent(g->copy_stream, used[bi], 0);  // chunk k-nbuf consumed
                 cudaMemcpyAsync(stage_buf[bi], vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice,
@@ -904,7 +921,9 @@ vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capaci
     int64_t* rank_of = (int64_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 8);
     int64_t* d_off = on_device ? off_out : (int64_t*)sc.get((size_t)(Wn.ncell + 1) * 8);
     uint16_t* d_ids = on_device ? ids_out : (uint16_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 2);
-    float* d_vals = on_device ? vals_out : (float*)sc.get((size_t)std::max<int64_t>(M, 1) * 256);
+    // values into a page-locked host buffer: the gather kernel writes them in place
+    float* mapped = (!on_device && M > 0) ? static_cast<float*>(mapped_host(vals_out)) : nullptr;
+    float* d_vals = on_device ? vals_out : (mapped ? mapped : (float*)sc.get((size_t)std::max<int64_t>(M, 1) * 256));
     if (!rank_of || !d_off || !d_ids || !d_vals) return fail(g, VL_ENOMEM, "vl_get_blocks: scratch allocation failed");
     k_offsets64<<<nblk(Wn.ncell + 1, 256), 256, 0, s>>>(cexc, cbase, chunk, Wn.ncell, d_off); note_launch();
     k_fill_ids<<<nblk(Wn.ncell, 128), 128, 0, s>>>(G, Wn, L.view(), d_off, d_ids, rank_of); note_launch();
@@ -918,7 +937,7 @@ vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capaci
         cudaMemcpyAsync(off_out, d_off, (size_t)(Wn.ncell + 1) * 8, cudaMemcpyDeviceToHost, s);
         if (M > 0) {
             cudaMemcpyAsync(ids_out, d_ids, (size_t)M * 2, cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(vals_out, d_vals, (size_t)M * 256, cudaMemcpyDeviceToHost, s);
+            if (!mapped) cudaMemcpyAsync(vals_out, d_vals, (size_t)M * 256, cudaMemcpyDeviceToHost, s);
         }
     }
     e = cudaStreamSynchronize(s);

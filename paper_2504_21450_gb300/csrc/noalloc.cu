@@ -1,9 +1,8 @@
 // noalloc.cu -- a translation step that allocates no memory.
 //
-// Some callers cannot allocate device memory: code that runs inside a CUDA graph
-// capture region or under a strict memory budget owned by another runtime, embedded
-// hosts whose allocator is not reachable from this library, or callers that must not
-// touch the device heap between two steps.  For them vl_translate_dense_noalloc runs
+// Some callers cannot allocate device memory: code that runs under a strict memory
+// budget owned by another runtime, embedded hosts whose allocator is not reachable from
+// this library, or callers that must not touch the device heap between two steps.  For them vl_translate_dense_noalloc runs
 // the fused Ghost Translation kernel on caller-provided input and output buffers of a
 // dense velocity space, and keeps everything else the kernel needs (its work list,
 // layout tables, sweep constants and counters) in one statically sized device array
@@ -21,7 +20,8 @@ namespace {
 
 using namespace vlgt;
 
-constexpr size_t kScratchBytes = (size_t)1 << 20;  // VL_NOALLOC_SCRATCH_BYTES in vlasov.h
+constexpr size_t kScratchBytes = VL_NOALLOC_SCRATCH_BYTES;  // the limit promised in vlasov.h
+static_assert(kScratchBytes % 256 == 0, "scratch size must keep the 256-byte sub-array alignment");
 
 // The scratch of the allocation-free entry point.  Host code must not take its address
 // directly (that is a host-side stand-in, not a device address): setup() asks the

@@ -305,3 +305,60 @@ def test_blocks_straddling_zero_velocity(vmin):
         g.close()
     for a, b in zip(*outs):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("form", ["fused", "3pass"])
+def test_mass_and_dropped_mass_with_non_unit_cells(form):
+    """Unequal, non-unit cell sizes along every axis (the oracle's volume factor is
+    pinned on the same state): every cell holds a block of value 0.75 and one of 0.25;
+    with threshold 0.5 and dt = 0 the step drops the second, and the FP64 mass and
+    dropped mass equal f times the phase-space volume they cover, which the binary
+    fractions make exact."""
+    n, dx = (3, 4, 5), (0.5, 1.5, 2.0)
+    mesh = oracle.Mesh(n=n, nv=(8, 4, 4), vmin=(-1.0, 0.0, -8.0), dv=(0.25, 0.5, 2.0), dx=dx)
+    ncell = int(np.prod(n))
+    off = np.arange(ncell + 1, dtype=np.int64) * 2
+    ids = np.tile(np.array([0, 1], dtype=np.uint16), ncell)
+    vals = np.empty((2 * ncell, 64), dtype=np.float32)
+    vals[0::2], vals[1::2] = 0.75, 0.25
+    volume = 90.0 * 32.0  # spatial box volume x velocity box volume
+    g = gpu_grid(mesh, 0.5)
+    g.set_blocks(off, ids, vals)
+    assert g.mass() == 0.5 * volume
+    assert g.mass() == oracle.mass(mesh, oracle.as_blocks(off, ids, vals.astype(np.float64)))
+    g.translate(0.0, "xyz", 1, FORMS[form], check=True)
+    s = g.stats()
+    assert s.dropped_mass == 0.25 * volume / 2 and s.mass == 0.75 * volume / 2
+    assert g.mass() == 0.75 * volume / 2 and g.block_count() == ncell
+    g.close()
+
+
+@pytest.mark.parametrize("storage", [vlasov.VL_STORE_F32, vlasov.VL_STORE_F16_SCALED])
+def test_page_locked_host_buffers_are_read_and_written_in_place(storage):
+    """vl_set_blocks from page-locked host memory (read in place by the scatter kernel)
+    and vl_get_blocks into page-locked host memory (written in place by the gather
+    kernel) give the same state as the staged paths from pageable numpy buffers."""
+    import torch
+    n = (21, 13, 9)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.4, seed=95)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    a = vlasov.Grid(mesh.n, mesh.nv, mesh.vmin, mesh.dv, mesh.dx, threshold=0.1, storage=storage)
+    a.set_blocks(init.off, init.ids, init.vals)
+    a.translate(0.2, "xyz", 1, check=True)
+    want = a.get_blocks()
+    h_off = torch.from_numpy(init.off.copy()).pin_memory()
+    h_ids = torch.from_numpy(init.ids.astype(np.int16)).pin_memory()
+    h_vals = torch.from_numpy(init.vals.copy()).pin_memory()
+    b = vlasov.Grid(mesh.n, mesh.nv, mesh.vmin, mesh.dv, mesh.dx, threshold=0.1, storage=storage)
+    vlasov.vl_set_blocks(b.handle, int(init.ids.size), h_off.data_ptr(), h_ids.data_ptr(), h_vals.data_ptr(), 0)
+    b.translate(0.2, "xyz", 1, check=True)
+    m = b.block_count()
+    o_off = torch.zeros(b.ncells + 1, dtype=torch.int64).pin_memory()
+    o_ids = torch.zeros(m, dtype=torch.int16).pin_memory()
+    o_vals = torch.full((m, 64), float("nan"), dtype=torch.float32).pin_memory()
+    vlasov.vl_get_blocks(b.handle, m, o_off.data_ptr(), o_ids.data_ptr(), o_vals.data_ptr(), 0)
+    np.testing.assert_array_equal(o_off.numpy(), want[0])
+    np.testing.assert_array_equal(o_ids.numpy().astype(np.uint16), want[1])
+    np.testing.assert_array_equal(o_vals.numpy(), want[2])
+    a.close()
+    b.close()
