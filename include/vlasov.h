@@ -137,7 +137,7 @@ typedef struct {
                        the remaining steps run again.  The graph is cached and replayed
                        by later calls with the same step count, form, order and pools. */
     int kernel;     /* fused form, which kernel: 0 (default) the plane-batched kernel (16 x 16
-                       tiles) where it applies -- FP32 storage, GT3, streamed axis y or z, no
+                       tiles) where it applies -- GT3, streamed axis y or z, no
                        velocity block straddling v_d = 0, tile[1] = 0 -- else the row-segment
                        kernel; 1 the plane-batched kernel (VL_EINVAL where it does not
                        apply); 2 the row-segment kernel (tile rows from tile[1]) */

@@ -867,7 +867,7 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
     a.kernel = opts.kernel;
     if (opts.kernel == 1 && opts.form != VL_FORM_3PASS && !gt3_applies(g, a))
         return fail(g, VL_EINVAL,
-                    "vl_translate: the plane-batched kernel needs FP32 storage, GT3, a streamed axis y or z "
+                    "vl_translate: the plane-batched kernel needs GT3, a streamed axis y or z "
                     "and no velocity block straddling v_d = 0");
     if (!g->ev_sweep0) {
         cudaEventCreate(&g->ev_sweep0);

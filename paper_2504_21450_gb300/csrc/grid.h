@@ -201,7 +201,7 @@ struct TileArgs {
     int ty;
 };
 void launch_tile_list(Grid* g, const TileArgs& T, int64_t need, int64_t ntiles);
-// gt3.cu: the plane-batched GT3 kernel (FP32 storage, GT3, streamed axis y or z, no
+// gt3.cu: the plane-batched GT3 kernel (GT3, streamed axis y or z, no
 // velocity block straddling v_d = 0)
 bool gt3_applies(const Grid* g, const StepArgs& a);
 vl_status run_gt3(Grid* g, const StepArgs& a);

@@ -53,6 +53,7 @@ struct Gt3Smem {
     float4 kc[3][kChunk];     // WalkConst (g, A, B, up) per sweep and velocity cell
     int run[2][kE][3];        // per item parity: contiguous runs of a staged row along x
     int rrow[2][kE];          // per item parity: row-space part of each staged row
+    int xs[2][kE];            // per item parity: x of each staged column
     uint64_t bar[2];          // staging barriers, one per batch buffer
     long long work;           // the current work item
     long long next;           // the one after it (taken while the current one runs)
@@ -136,6 +137,43 @@ __device__ __forceinline__ void copy_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// 16-byte copy global -> shared; src_bytes = 0 fills the 16 bytes with zeros
+__device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+// the barrier's pending count drops by one once this thread's earlier cp.async copies land
+__device__ __forceinline__ void cp_arrive(uint64_t* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(su32(bar)) : "memory");
+}
+
+// Two 16-bit codes (lanes l, l+1) as floats times the block id's scale, as Codec::dec
+// does per value (the scale is a power of two: exact).
+template <int kCodec>
+__device__ __forceinline__ float2 dec2(uint32_t w, float2 s)
+{
+    float2 f;
+    if constexpr (kCodec == 1) f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    else f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    return mul2(f, s);
+}
+// Two floats times 1/scale rounded to 16-bit codes, as Codec::enc does per value.
+template <int kCodec>
+__device__ __forceinline__ uint32_t enc2(float2 f, float2 inv)
+{
+    const float2 x = mul2(f, inv);
+    uint32_t w;
+    if constexpr (kCodec == 1) {
+        const __nv_bfloat162 h = __float22bfloat162_rn(x);
+        w = *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __half2 h = __float22half2_rn(x);
+        w = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return w;
+}
 
 // A staging wait gives up after one second of device time or 2^24 polls (a batch is a
 // few tens of kB staged in microseconds): reaching either means a fault upstream.
@@ -196,10 +234,12 @@ __device__ __forceinline__ Item decode_item(const Gt3Args& P, int64_t w)
     return it;
 }
 
-// Runs and row parts of an item's staged rows into table t (threads kNC-1-kE .. kNC-1).
+// Runs and row parts of an item's staged rows and the x of its staged columns into
+// table t (threads kNC-1-2kE .. kNC-1).
 __device__ __forceinline__ void item_tables(const Gt3Args& P, Gt3Smem& S, const Item& it, int t, int tid)
 {
     const int nx = P.G.n[0], nr = P.G.n[P.ar];
+    if (tid >= kNC - 1 - 2 * kE && tid < kNC - 1 - kE) S.xs[t][tid - (kNC - 1 - 2 * kE)] = wrapi(it.tx0 - kHalo + tid - (kNC - 1 - 2 * kE), nx);
     if (tid == kNC - 1) {
         int u0 = 0, nrun = 0;
         while (u0 < kE) {
@@ -220,6 +260,12 @@ __device__ __forceinline__ void item_tables(const Gt3Args& P, Gt3Smem& S, const 
 
 // Staging of batch k of an item (planes kNB k .. kNB k + 2 of its stream) into buffer
 // g & 1, g = the CTA's running batch index; run by the kNS staging threads (sl = 0..127).
+// FP32 storage: TMA bulk copies of contiguous runs.  16-bit storage: the 32 bytes of
+// codes of each staged cell go to the upper half of its 64-byte slot with two 16-byte
+// cp.async copies (sweep 0 decodes them and writes its FP32 result into the slot of the
+// cell two positions behind, whose codes it has already read), and every staging
+// thread arrives on the barrier once its copies have landed.
+template <int kCodec>
 __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const Item& it, int t, int k,
                                             unsigned g, int sl)
 {
@@ -233,7 +279,30 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
     const float* ipool = static_cast<const float*>(P.in.pool);
     auto plane_of = [&](int s) { return it.up2 ? s - kHalo : n2 + 2 - s; };
     auto out_of = [&](int s) { return it.up2 ? s - kFirst : n2 + 4 - s; };
-    if (it.dense_in) {
+    if constexpr (kCodec != 0) {
+        using T = typename Codec<kCodec>::T;
+        const T* cpool = static_cast<const T*>(P.in.pool);
+        const int npiece = nj * kE * kE * 2;
+        for (int i = sl; i < npiece; i += kNS) {
+            const int piece = i & 1, c = i >> 1;
+            const int u = c % kE, rr = c / kE;
+            const int rho = rr % kE, j = rr / kE;
+            const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, wrapi(plane_of(kNB * k + j), n2), ny);
+            const int x = S.xs[t][u];
+            int64_t r;
+            if (it.dense_in) {
+                r = row * nx + x;
+            } else {
+                const int64_t wi = (int64_t)it.b * G.RW + row * G.W + (x >> 6);
+                const uint64_t bit = 1ull << (x & 63);
+                const uint64_t uw = P.in.ubits[wi];
+                r = ((uw & P.in.kbits[wi] & bit) != 0ull) ? (int64_t)P.in.woff[wi] + __popcll(uw & (bit - 1ull)) : -1;
+            }
+            float* dst = &S.buf[slot][j][rho * kRP + u * kChunk + 8 + 4 * piece];
+            cp16(dst, r >= 0 ? cpool + it.ibase + r * kChunk + 8 * piece : cpool, r >= 0 ? 16 : 0);
+        }
+        cp_arrive(bar);
+    } else if (it.dense_in) {
         // one arrival carrying the batch's bytes; the copies of the other staging
         // threads may complete before or after it
         if (sl == 0) bar_arrive_tx(bar, (unsigned)(nj * kE * kE * kChunk * sizeof(float)));
@@ -324,7 +393,7 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
     }
 }
 
-template <bool kLim, bool kA0X>
+template <bool kLim, bool kA0X, int kCodec>
 __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -346,8 +415,9 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
     constexpr int kS1 = kA0X ? kRP : kChunk;
 
     if (tid == 0) {
-        bar_init(&S.bar[0], 1);
-        bar_init(&S.bar[1], 1);
+        // FP32: one arrival (with the batch's bytes); 16-bit: one per staging thread
+        bar_init(&S.bar[0], kCodec ? kNS : 1);
+        bar_init(&S.bar[1], kCodec ? kNS : 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         S.abort = 0;
         S.pref = 0;
@@ -365,7 +435,15 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
         const int ti = (int)(ni & 1u);
         const Item it = decode_item(P, w);
         const int64_t okeep = (int64_t)P.out.base[it.b];
-        float* opool = static_cast<float*>(P.out.pool);
+        using T = typename Codec<kCodec>::T;
+        T* opool = static_cast<T*>(P.out.pool);
+        // 16-bit storage: scales of the codes read and written (powers of two)
+        const float sc_in = kCodec ? P.in.scale[it.b] : 1.0f;
+        const float sc_out = kCodec ? P.out.scale[it.b] : 1.0f;
+        const float2 sc_in2 = make_float2(sc_in, sc_in);
+        const float2 sc_out2 = make_float2(sc_out, sc_out);
+        const float2 inv_out2 = make_float2(1.0f / sc_out, 1.0f / sc_out);
+        float vmx = 0.0f;  // largest |stored value| of this item (16-bit storage)
         if (!pref) item_tables(P, S, it, ti, tid);
         if (tid < 3 * kChunk) {
             // sweep constants of the item's 16 velocity cells (v = vx + 4 vy, vz = q)
@@ -374,7 +452,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             const int bc = d == 0 ? it.b % G.nbx : (d == 1 ? (it.b / G.nbx) % G.nby : it.b / (G.nbx * G.nby));
             const int wi = d == 0 ? (l & 3) : (d == 1 ? (l >> 2) : it.q);
             S.kc[j][l] = P.walk[d * P.nvmax + bc * 4 + wi];
-        } else if (tid == kNC - 2 - kE) {
+        } else if (tid == 64) {
             S.next = (long long)atomicAdd(&P.ctr->work_next, 1ull);
         }
         __syncthreads();  // per-item tables ready
@@ -403,7 +481,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             kz.B = make_float2(c.z, c.z);
         }
 
-        if (stager && !pref) stage_batch(P, S, it, ti, 0, gb, sl);
+        if (stager && !pref) stage_batch<kCodec>(P, S, it, ti, 0, gb, sl);
         int k = 0;
         for (; k < nbatch; k++) {
             const unsigned slot = (gb + k) & 1u;
@@ -423,18 +501,24 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                     const float4 c0 = S.kc[0][l0], c1 = S.kc[0][l0 + 1];
                     const WalkConst2 kx{make_float2(c0.x, c1.x), make_float2(c0.y, c1.y), make_float2(c0.z, c1.z)};
                     float* p = B + j * kPS + (line + (up1 ? 0 : 1)) * kS1 + l0;
+                    // the two staged values of position m: FP32, or two 16-bit codes in the
+                    // upper half of the cell's slot
+                    auto in = [&](int m) -> float2 {
+                        if constexpr (kCodec == 0) return lds2(p + m * kS0);
+                        else return dec2<kCodec>(reinterpret_cast<const uint32_t*>(p - l0 + m * kS0)[8 + (l0 >> 1)], sc_in2);
+                    };
                     Walk2<kLim> wk;
                     wk.reset();
                     if (up0) {
 #pragma unroll
                         for (int m = 0; m < kLines; m++) {
-                            const float2 r = wk.push(lds2(p + m * kS0), kx);
+                            const float2 r = wk.push(in(m), kx);
                             if (m >= 5) sts2(p + (m - 2) * kS0, r);
                         }
                     } else {
 #pragma unroll
                         for (int m = 0; m < kLines; m++) {
-                            const float2 r = wk.push(lds2(p + (kLines - m) * kS0), kx);
+                            const float2 r = wk.push(in(kLines - m), kx);
                             if (m >= 5) sts2(p + (kLines + 2 - m) * kS0, r);
                         }
                     }
@@ -444,7 +528,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             if (S.abort) break;
             if (stager) {
                 if (k + 1 < nbatch) {
-                    stage_batch(P, S, it, ti, k + 1, gb + k + 1, sl);
+                    stage_batch<kCodec>(P, S, it, ti, k + 1, gb + k + 1, sl);
                 } else {
                     // last batch: stage the first batch of the next item
                     const int64_t wn = S.next;
@@ -452,7 +536,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                         const Item nx = decode_item(P, wn);
                         item_tables(P, S, nx, ti ^ 1, tid);
                         asm volatile("bar.sync 1, %0;\n" ::"n"(kNS) : "memory");
-                        stage_batch(P, S, nx, ti ^ 1, 0, gb + nbatch, sl);
+                        stage_batch<kCodec>(P, S, nx, ti ^ 1, 0, gb + nbatch, sl);
                         if (sl == 0) S.pref = 1;
                     }
                 }
@@ -509,17 +593,31 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                 }
                 float psum = 0.0f;
                 bool keep0 = false, keep1 = false;
+                // store one vx row (4 values) of a cell; v0, v1 become the values the state
+                // now holds (16-bit storage: the codes decoded)
+                auto store = [&](int64_t rk, float2& v0, float2& v1) {
+                    T* dst = opool + it.obase + rk * kChunk + 4 * zq;
+                    if constexpr (kCodec == 0) {
+                        *reinterpret_cast<float4*>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                    } else {
+                        const uint32_t w0 = enc2<kCodec>(v0, inv_out2), w1 = enc2<kCodec>(v1, inv_out2);
+                        *reinterpret_cast<uint2*>(dst) = make_uint2(w0, w1);
+                        v0 = dec2<kCodec>(w0, sc_out2);
+                        v1 = dec2<kCodec>(w1, sc_out2);
+                        vmx = fmaxf(vmx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                    }
+                };
                 if (rk0 >= 0) {
-                    *reinterpret_cast<float4*>(opool + it.obase + rk0 * kChunk + 4 * zq) =
-                        make_float4(r00.x, r00.y, r01.x, r01.y);
-                    psum += (r00.x + r00.y) + (r01.x + r01.y);
-                    keep0 = fmaxf(fmaxf(r00.x, r00.y), fmaxf(r01.x, r01.y)) >= P.thr;
+                    float2 v0 = r00, v1 = r01;
+                    store(rk0, v0, v1);
+                    psum += (v0.x + v0.y) + (v1.x + v1.y);
+                    keep0 = fmaxf(fmaxf(v0.x, v0.y), fmaxf(v1.x, v1.y)) >= P.thr;
                 }
                 if (rk1 >= 0) {
-                    *reinterpret_cast<float4*>(opool + it.obase + rk1 * kChunk + 4 * zq) =
-                        make_float4(r10.x, r10.y, r11.x, r11.y);
-                    psum += (r10.x + r10.y) + (r11.x + r11.y);
-                    keep1 = fmaxf(fmaxf(r10.x, r10.y), fmaxf(r11.x, r11.y)) >= P.thr;
+                    float2 v0 = r10, v1 = r11;
+                    store(rk1, v0, v1);
+                    psum += (v0.x + v0.y) + (v1.x + v1.y);
+                    keep1 = fmaxf(fmaxf(v0.x, v0.y), fmaxf(v1.x, v1.y)) >= P.thr;
                 }
                 // per-chunk keep flags: the four threads of a cell vote
                 const unsigned b0 = __ballot_sync(0xffffffffu, keep0);
@@ -546,6 +644,10 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             if (tid == 0 && k < nbatch) bar_wait_bounded(&S.bar[(gb + k) & 1u], ((gb + k) >> 1) & 1u);
             break;
         }
+        if (kCodec) {
+            const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
+            if (lane == 0 && u) atomicMax(&P.out.vmax[it.b], u);
+        }
         gb += (unsigned)nbatch;
     }
     double m = (double)msum;
@@ -555,10 +657,10 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
     if (P.cta_done && tid == 0) P.cta_done[blockIdx.x] = now_ns();
 }
 
-template <bool kLim, bool kA0X>
+template <bool kLim, bool kA0X, int kCodec>
 vl_status launch_gt3(Grid* g, const Gt3Args& P)
 {
-    auto kern = k_gt3<kLim, kA0X>;
+    auto kern = k_gt3<kLim, kA0X, kCodec>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
@@ -578,7 +680,7 @@ inline int nblocks_of(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 bool gt3_applies(const Grid* g, const StepArgs& a)
 {
-    if (a.ghost != 3 || g->codec != 0) return false;
+    if (a.ghost != 3) return false;
     if (a.order[2] == 0) return false;  // streamed axis must not be x
     // every velocity block moves one way along each axis
     for (int d = 0; d < 3; d++)
@@ -642,9 +744,12 @@ vl_status run_gt3(Grid* g, const StepArgs& a)
     P.cta_done = a.stamp_ctas ? g->cta_done : nullptr;
     record_sweep_event(a.ev0, g->stream, a.ev_node);
     const bool a0x = a.order[0] == 0;
-    vl_status st;
-    if (a0x) st = a.limiter ? launch_gt3<true, true>(g, P) : launch_gt3<false, true>(g, P);
-    else st = a.limiter ? launch_gt3<true, false>(g, P) : launch_gt3<false, false>(g, P);
+    vl_status st = VL_OK;
+    with_codec(g->codec, [&](auto c) {
+        constexpr int kc = decltype(c)::value;
+        if (a0x) st = a.limiter ? launch_gt3<true, true, kc>(g, P) : launch_gt3<false, true, kc>(g, P);
+        else st = a.limiter ? launch_gt3<true, false, kc>(g, P) : launch_gt3<false, false, kc>(g, P);
+    });
     record_sweep_event(a.ev1, g->stream, a.ev_node);
     (void)nblocks_of;
     return st;

@@ -144,3 +144,26 @@ def test_default_kernel_and_where_it_does_not_apply():
             g.translate(0.2, order, 1, vlasov.VL_FORM_FUSED, kernel=BATCHED)
         assert e.value.status == vlasov.VL_EINVAL
         g.close()
+
+
+@pytest.mark.parametrize("storage", [vlasov.VL_STORE_BF16_SCALED, vlasov.VL_STORE_F16_SCALED])
+@pytest.mark.parametrize("order", ["xyz", "yxz"])
+def test_batched_16bit_storage_equals_row_segment_kernel(storage, order):
+    """Scaled 16-bit storage: both fused kernels decode the stored codes, run the same
+    per-velocity-cell arithmetic in FP32 and round once per step with the same scale,
+    so their states, codes included, agree bit for bit; sparse blocks and pruning."""
+    n = (37, 19, 11)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.35, seed=96)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    outs = []
+    for kernel in (BATCHED, ROWS):
+        g = vlasov.Grid(mesh.n, mesh.nv, mesh.vmin, mesh.dv, mesh.dx, threshold=0.05, storage=storage)
+        g.set_blocks(init.off, init.ids, init.vals)
+        g.translate(0.2, order, 2, vlasov.VL_FORM_FUSED, check=True, kernel=kernel,
+                    tile_rows=0 if kernel == BATCHED else 16)
+        assert g.stats().kernel_used == kernel
+        outs.append((g.get_blocks(), g.export()))
+        g.close()
+    for x, y in zip(outs[0][0], outs[1][0]):
+        np.testing.assert_array_equal(x, y)
+    assert outs[0][1] == outs[1][1]  # checkpoints: codes, scales and maxima
