@@ -305,7 +305,8 @@ def run_ours(args, cfg):
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        quiet_nccl()
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     form = {"fused": vlasov.VL_FORM_FUSED, "3pass": vlasov.VL_FORM_3PASS,
             "auto": vlasov.VL_FORM_AUTO}[args.form]
     storage = {"f32": vlasov.VL_STORE_F32, "bf16": vlasov.VL_STORE_BF16_SCALED,
@@ -503,6 +504,107 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
+def quiet_nccl():
+    """Rank 0 prints one JSON line on stdout: keep NCCL's version banner off it unless the
+    user asked for NCCL's own logging."""
+    if os.environ.get("NCCL_DEBUG", "VERSION").upper() == "VERSION":
+        os.environ["NCCL_DEBUG"] = "WARN"
+
+
+def run_slab(args, cfg):
+    """N > 1 GPUs: the spatial domain split into z-slabs over the ranks (weak scaling: each
+    rank owns the per-GPU workload's nz planes of a global grid of nz * N planes).  A timed
+    step is one coalesced ghost update (3 planes from each neighbour over NCCL, Section 3)
+    followed by one translation step of each rank's local grid (its planes plus 3 ghost
+    planes on either side)."""
+    import dataclasses
+
+    import torch
+    import torch.distributed as dist
+    from paper_2504_21450_gb300 import slab, vlasov
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if "MASTER_ADDR" not in os.environ:  # one rank started without a launcher
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=os.environ.get("MASTER_PORT", "29517"),
+                          RANK="0", WORLD_SIZE="1")
+    quiet_nccl()
+    dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    form = {"fused": vlasov.VL_FORM_FUSED, "3pass": vlasov.VL_FORM_3PASS,
+            "auto": vlasov.VL_FORM_AUTO}[args.form]
+    storage = {"f32": vlasov.VL_STORE_F32, "bf16": vlasov.VL_STORE_BF16_SCALED,
+               "f16": vlasov.VL_STORE_F16_SCALED}[args.storage]
+    kern = KERNEL_OPT[args.kernel]
+    gcfg = dataclasses.replace(cfg, n=(cfg.n[0], cfg.n[1], cfg.n[2] * world), name=f"{cfg.name}-slabs{world}")
+    sl = slab.slabs(gcfg.n[2], world)[rank]
+    ln = (cfg.n[0], cfg.n[1], sl.local_nz)
+    off, ids, vals, thr = inputs.generate_torch(gcfg, f"cuda:{local}", origin=(0, 0, sl.origin_z), size=ln)
+    g = vlasov.Grid(ln, cfg.nv, cfg.vmin, cfg.dv, cfg.dx, threshold=thr, storage=storage, device=local)
+    g.set_blocks(off, ids, vals)
+    del off, ids, vals
+    torch.cuda.empty_cache()
+    planes = slab.GridPlanes(g)
+    ex = slab.TorchExchange(sl, dist, f"cuda:{local}")
+    owned_window = ((0, 0, slab.GHOST), (ln[0], ln[1], sl.owned))
+
+    def step():
+        slab.ghost_update(sl, planes.get, planes.set, ex)
+        g.translate(cfg.dt, args.order, 1, form, ghost=args.ghost, kernel=kern)
+
+    for _ in range(max(args.warmup, 8 if form == vlasov.VL_FORM_AUTO else 0)):
+        step()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    updates = 0
+    sweep_ms = 0.0
+    launches = 0
+    local_updates = 0
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            updates += vlasov.vl_get_block_count_window(g.handle, *owned_window) * 64
+            step()
+            s = g.stats()
+            sweep_ms += s.sweep_ms
+            launches += s.launches
+            local_updates += s.updates
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    el_ms, total_updates = aggregate(ev0.elapsed_time(ev1), updates, dist, "cuda")
+    peak, peak_kind = measured_peak_hbm()
+    form_used = {vlasov.VL_FORM_FUSED: "fused", vlasov.VL_FORM_3PASS: "3pass"}.get(s.form_used, "fused")
+    kernel_key = "fused-rows" if (form_used == "fused" and int(s.kernel_used) == 2) else form_used
+    launches_sweep = LAUNCHES_PER_STEP[form_used] * args.steps
+    avg_launch_s = (sweep_ms / launches_sweep) / 1e3 if sweep_ms > 0 else float("nan")
+    bytes_per_update = BYTES_PER_UPDATE[form_used] * STORAGE_BYTES[args.storage] / 4
+    achieved = bytes_per_update * (local_updates / args.steps) / avg_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": total_updates / (el_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(gcfg), "form": form_used, "kernel": KERNEL[kernel_key],
+                   "storage": args.storage, "order": args.order, "parallelism": f"slabs{world}",
+                   "decomposition": {"axis": "z", "owned_planes_rank0": sl.owned,
+                                     "ghost_planes": 2 * slab.GHOST, "exchange": "NCCL send/recv, once per step"},
+                   "l2": "state larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "kernel": KERNEL[kernel_key],
+                     "traffic": None, "avg_launch_ms": avg_launch_s * 1e3,
+                     "note": "local grid (owned and ghost planes) per launch"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": {"value": None, "unit": UNIT, "note": "not measured in the slab decomposition"},
+    }
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,6 +633,10 @@ def main():
                          "union count + 25%%, or the learned cost model")
     ap.add_argument("--chunk", type=int, default=0, help="steps per captured call (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--decomp", default="auto", choices=["auto", "slabs", "replicas"],
+                    help="auto: z-slabs with one ghost update per step when N > 1, else one "
+                         "domain; slabs: the slab path also for one rank (its own planes are its "
+                         "ghosts); replicas: N independent copies of the workload")
     args = ap.parse_args()
     if args.ghost != 3 and args.form != "fused":
         ap.error("--ghost 1 or 2 needs --form fused (GT1/GT2 exist in the fused form only)")
@@ -540,6 +646,8 @@ def main():
         cfg = dataclasses.replace(cfg, n=tuple(args.grid), name=f"{cfg.name}-{'x'.join(map(str, args.grid))}")
     if args.impl == "reference":
         run_reference(args, cfg)
+    elif args.decomp == "slabs" or (args.decomp == "auto" and dist_env()[1] > 1):
+        run_slab(args, cfg)
     else:
         run_ours(args, cfg)
 

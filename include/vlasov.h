@@ -214,6 +214,21 @@ vl_status vl_get_block_count(vl_grid* grid, int64_t* nblocks);
 vl_status vl_get_blocks(vl_grid* grid, int64_t capacity, int64_t* cell_offsets,
                         uint16_t* block_ids, float* values, int on_device);
 
+/* Replace the blocks of the z-planes z0 .. z0+nplanes-1 (wrapping periodically) by the
+ * given per-cell lists and keep every other cell: the ghost update of a decomposition of
+ * the spatial domain into z-slabs (Section 3: one coalesced ghost update per step, from
+ * the neighbours' boundary planes, which vl_get_blocks_window reads).  The lists cover
+ * nx*ny*nplanes cells in window order (x fastest, then y, then the planes in order),
+ * nblocks = cell_offsets[nx*ny*nplanes]; on_device as in vl_set_blocks.  When the
+ * lists hold exactly the blocks the window already holds (with FP32 storage), their
+ * values are written into the existing slots (work of the order of the window);
+ * otherwise the layout is rebuilt from the whole state's lists on the device (work and
+ * scratch memory of the order of the state; with 16-bit storage the codes are rounded
+ * again with the scales of the new state).  Errors: VL_ESTATE (no state), VL_EINVAL, VL_ENOMEM, VL_ECUDA. */
+vl_status vl_set_blocks_planes(vl_grid* grid, int z0, int nplanes, int64_t nblocks,
+                               const int64_t* cell_offsets, const uint16_t* block_ids,
+                               const float* values, int on_device);
+
 /* Per-cell lists of a box window: the cells origin[d] + [0, size[d]) (wrapping
  * periodically), x fastest, 1 <= size[d] <= n[d].  Same formats, ownership and errors as
  * vl_get_blocks; cell_offsets has size[0]*size[1]*size[2]+1 entries.  Used to sample a

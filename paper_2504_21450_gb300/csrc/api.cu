@@ -656,6 +656,16 @@ vl_status vl_get_block_count_window(vl_grid* grid, const int origin[3], const in
     return get_window(g, origin, size, 0, nullptr, nullptr, nullptr, 0, nblocks);
 }
 
+vl_status vl_set_blocks_planes(vl_grid* grid, int z0, int nplanes, int64_t nblocks,
+                               const int64_t* cell_offsets, const uint16_t* block_ids,
+                               const float* values, int on_device)
+{
+    if (!grid) return VL_EINVAL;
+    Grid* g = reinterpret_cast<Grid*>(grid);
+    DeviceGuard dg(g->dev.device);
+    return set_blocks_planes(g, z0, nplanes, nblocks, cell_offsets, block_ids, values, on_device);
+}
+
 vl_status vl_get_blocks_window(vl_grid* grid, const int origin[3], const int size[3],
                                int64_t capacity, int64_t* cell_offsets, uint16_t* block_ids,
                                float* values, int on_device)

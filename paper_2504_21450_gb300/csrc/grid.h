@@ -126,6 +126,10 @@ vl_status set_blocks(Grid* g, int64_t nblocks, const int64_t* off, const uint16_
                      const float* vals, int on_device, const float* scale_host = nullptr,
                      const unsigned* vmax_host = nullptr);
 vl_status get_block_count(Grid* g, int64_t* n);
+// Replaces the blocks of z-planes z0 .. z0+nplanes-1 (wrapping) by the given lists (in
+// window order) and keeps every other cell.
+vl_status set_blocks_planes(Grid* g, int z0, int nplanes, int64_t nblocks, const int64_t* off,
+                            const uint16_t* ids, const float* vals, int on_device);
 vl_status get_blocks(Grid* g, int64_t capacity, int64_t* off, uint16_t* ids, float* vals,
                      int on_device);
 vl_status get_window(Grid* g, const int* origin, const int* size, int64_t capacity,

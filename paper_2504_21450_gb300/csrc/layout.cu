@@ -957,6 +957,173 @@ vl_status get_blocks(Grid* g, int64_t capacity, int64_t* off_out, uint16_t* ids_
     return get_window(g, nullptr, nullptr, capacity, off_out, ids_out, vals_out, on_device, nullptr);
 }
 
+namespace {
+// Window block t -> its cell in the grid (planes from z0, wrapping); err |= 1 when the
+// cell does not hold that block id in the current layout, 2 when the id is out of range.
+__global__ void k_window_cells(GridGeom G, LayoutView L, const int64_t* __restrict__ off_w, int64_t nw,
+                               const uint16_t* __restrict__ ids_w, int64_t Mw, int z0,
+                               int64_t* __restrict__ cell_of, int* err)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Mw) return;
+    const int64_t wc = cell_of_block(off_w, nw, t);
+    const int64_t nxy = (int64_t)G.n[0] * G.n[1];
+    const int64_t c = wc % nxy + (int64_t)wrapi(z0 + (int)(wc / nxy), G.n[2]) * nxy;
+    const int b = ids_w[t];
+    if (b >= G.nb) {
+        atomicOr(err, 2);
+        return;
+    }
+    cell_of[t] = c;
+    const int x = (int)(c % G.n[0]);
+    const int64_t wi = (int64_t)b * G.RW + (c / G.n[0]) * G.W + (x >> 6);
+    if (!((L.kbits[wi] >> (x & 63)) & 1ull)) atomicOr(err, 1);
+}
+
+// dst_off[d0 + i] = src_off[s0 + i] - src_off[s0] + base, i = 0 .. n-1
+__global__ void k_shift_offsets(const int64_t* __restrict__ src_off, int64_t s0, int64_t n, int64_t base,
+                                int64_t* __restrict__ dst_off, int64_t d0)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst_off[d0 + i] = src_off[s0 + i] - src_off[s0] + base;
+}
+}  // namespace
+
+// Replaces the blocks of z-planes z0 .. z0+nplanes-1 (wrapping) by the window lists and
+// keeps every other cell.  A set of whole z-planes is one or two contiguous ranges of
+// the cell order (x fastest, then y, then z), so the new lists are runs of the old and
+// the window lists joined end to end: device copies of ids and values, shifted offsets,
+// then the layout rebuilt from the joined lists by set_blocks.
+vl_status set_blocks_planes(Grid* g, int z0, int nplanes, int64_t Mw, const int64_t* off_w_in,
+                            const uint16_t* ids_w_in, const float* vals_w_in, int on_device)
+{
+    const GridGeom& G = g->geom;
+    cudaStream_t s = g->stream;
+    if (!g->has_state) return fail(g, VL_ESTATE, "vl_set_blocks_planes: no state (call vl_set_blocks first)");
+    if (nplanes < 1 || nplanes > G.n[2] || Mw < 0 || !off_w_in || (Mw > 0 && (!ids_w_in || !vals_w_in)))
+        return fail(g, VL_EINVAL, "vl_set_blocks_planes: 1 <= nplanes <= nz, lists required");
+    const int64_t nxy = (int64_t)G.n[0] * G.n[1];
+    const int64_t nw = nxy * nplanes;
+    Scratch sc(g);
+    // the window lists on the device
+    const int64_t* off_w = off_w_in;
+    const uint16_t* ids_w = ids_w_in;
+    const float* vals_w = vals_w_in;
+    if (!on_device) {
+        int64_t* a = (int64_t*)sc.get((size_t)(nw + 1) * 8);
+        uint16_t* b = (uint16_t*)sc.get((size_t)std::max<int64_t>(Mw, 1) * 2);
+        float* c = (float*)sc.get((size_t)std::max<int64_t>(Mw, 1) * 256);
+        if (!a || !b || !c) return fail(g, VL_ENOMEM, "vl_set_blocks_planes: staging allocation failed");
+        cudaMemcpyAsync(a, off_w_in, (size_t)(nw + 1) * 8, cudaMemcpyHostToDevice, s);
+        if (Mw > 0) {
+            cudaMemcpyAsync(b, ids_w_in, (size_t)Mw * 2, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(c, vals_w_in, (size_t)Mw * 256, cudaMemcpyHostToDevice, s);
+        }
+        off_w = a;
+        ids_w = b;
+        vals_w = c;
+    }
+    // fast path: the window keeps its block set (every listed block is present and the
+    // window holds as many), so the values go into their slots in place -- FP32 storage
+    // (16-bit codes may need new scales)
+    if (g->codec == 0) {
+        const int origin[3] = {0, 0, z0};
+        const int size[3] = {G.n[0], G.n[1], nplanes};
+        int64_t Mcur = -1;
+        vl_status st0 = get_window(g, origin, size, 0, nullptr, nullptr, nullptr, 0, &Mcur);
+        if (st0 != VL_OK) return st0;
+        if (Mcur == Mw) {
+            int64_t* cell_of = (int64_t*)sc.get((size_t)std::max<int64_t>(Mw, 1) * 8);
+            int* err = (int*)sc.get(sizeof(int));
+            if (!cell_of || !err) return fail(g, VL_ENOMEM, "vl_set_blocks_planes: scratch allocation failed");
+            Layout& L = g->lay[g->cur];
+            cudaMemsetAsync(err, 0, sizeof(int), s);
+            if (Mw > 0) {
+                k_window_cells<<<nblk(Mw, 256), 256, 0, s>>>(G, L.view(), off_w, nw, ids_w, Mw, z0, cell_of, err);
+                note_launch();
+            }
+            cudaMemcpyAsync(g->host_scalar, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks_planes");
+            const int herr = (int)(g->host_scalar[0] & 0xffffffff);
+            if (herr & 2) return fail(g, VL_EINVAL, "vl_set_blocks_planes: block id out of range of the velocity mesh");
+            if (herr == 0) {
+                if (Mw > 0) {
+                    k_scatter<0><<<nblk(Mw * 64, 256), 256, 0, s>>>(G, L.view(), ids_w, cell_of, vals_w, 0, Mw);
+                    note_launch();
+                }
+                e = cudaStreamSynchronize(s);
+                return e == cudaSuccess ? VL_OK : cuda_fail(g, e, "vl_set_blocks_planes");
+            }
+        }
+    }
+    // the whole current state as lists on the device
+    int64_t Mo = 0;
+    vl_status st = get_window(g, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0, &Mo);
+    if (st != VL_OK) return st;
+    int64_t* off_o = (int64_t*)sc.get((size_t)(G.N + 1) * 8);
+    uint16_t* ids_o = (uint16_t*)sc.get((size_t)std::max<int64_t>(Mo, 1) * 2);
+    float* vals_o = (float*)sc.get((size_t)std::max<int64_t>(Mo, 1) * 256);
+    if (!off_o || !ids_o || !vals_o) return fail(g, VL_ENOMEM, "vl_set_blocks_planes: scratch allocation failed");
+    st = get_window(g, nullptr, nullptr, Mo, off_o, ids_o, vals_o, 1, nullptr);
+    if (st != VL_OK) return st;
+    // runs in the new cell order: (source lists, first source cell, cells)
+    struct Run {
+        int kind;  // 0: old state, 1: window lists
+        int64_t s0, n;
+    };
+    const int64_t c0 = (int64_t)(((z0 % G.n[2]) + G.n[2]) % G.n[2]) * nxy;
+    const int64_t lenA = std::min(nw, G.N - c0);  // window cells before the wrap
+    std::vector<Run> runs;
+    if (lenA == nw) {
+        if (c0 > 0) runs.push_back({0, 0, c0});
+        runs.push_back({1, 0, nw});
+        if (c0 + nw < G.N) runs.push_back({0, c0 + nw, G.N - c0 - nw});
+    } else {
+        const int64_t cb = nw - lenA;  // window cells after the wrap, at cells 0 .. cb-1
+        runs.push_back({1, lenA, cb});
+        if (c0 > cb) runs.push_back({0, cb, c0 - cb});
+        runs.push_back({1, 0, lenA});
+    }
+    // block ranges of the runs (host copies of the offsets at the run bounds)
+    std::vector<int64_t> lo(runs.size()), hi(runs.size());
+    for (size_t i = 0; i < runs.size(); i++) {
+        const int64_t* off = runs[i].kind ? off_w : off_o;
+        cudaMemcpyAsync(&g->host_scalar[0], off + runs[i].s0, 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&g->host_scalar[1], off + runs[i].s0 + runs[i].n, 8, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks_planes");
+        lo[i] = g->host_scalar[0];
+        hi[i] = g->host_scalar[1];
+        if (hi[i] < lo[i]) return fail(g, VL_EINVAL, "vl_set_blocks_planes: cell offsets must be non-decreasing");
+    }
+    int64_t M = 0;
+    for (size_t i = 0; i < runs.size(); i++) M += hi[i] - lo[i];
+    int64_t* off_n = (int64_t*)sc.get((size_t)(G.N + 1) * 8);
+    uint16_t* ids_n = (uint16_t*)sc.get((size_t)std::max<int64_t>(M, 1) * 2);
+    float* vals_n = (float*)sc.get((size_t)std::max<int64_t>(M, 1) * 256);
+    if (!off_n || !ids_n || !vals_n) return fail(g, VL_ENOMEM, "vl_set_blocks_planes: scratch allocation failed");
+    int64_t d0 = 0, base = 0;
+    for (size_t i = 0; i < runs.size(); i++) {
+        const bool w = runs[i].kind != 0;
+        const int64_t nb = hi[i] - lo[i];
+        k_shift_offsets<<<nblk(runs[i].n, 256), 256, 0, s>>>(w ? off_w : off_o, runs[i].s0, runs[i].n, base, off_n, d0);
+        note_launch();
+        if (nb > 0) {
+            cudaMemcpyAsync(ids_n + base, (w ? ids_w : ids_o) + lo[i], (size_t)nb * 2, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(vals_n + base * 64, (w ? vals_w : vals_o) + lo[i] * 64, (size_t)nb * 256,
+                            cudaMemcpyDeviceToDevice, s);
+        }
+        d0 += runs[i].n;
+        base += nb;
+    }
+    g->host_scalar[0] = M;
+    cudaMemcpyAsync(off_n + G.N, &g->host_scalar[0], 8, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "vl_set_blocks_planes");
+    return set_blocks(g, M, off_n, ids_n, vals_n, 1);
+}
+
 vl_status moments(Grid* g, double* out, int on_device)
 {
     const GridGeom& G = g->geom;

@@ -91,6 +91,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "vl_translate": (i, [p, d, ctypes.c_char_p, i, p]),
         "vl_get_block_count_window": (i, [p, p, p, p]),
         "vl_get_blocks_window": (i, [p, p, p, i64, p, p, p, i]),
+        "vl_set_blocks_planes": (i, [p, i, i, i64, p, p, p, i]),
         "vl_moments": (i, [p, p, i]),
         "vl_mass": (i, [p, p]),
         "vl_stats": (i, [p, p]),
@@ -181,6 +182,12 @@ def vl_get_blocks_window(grid, origin, size, capacity: int, off_ptr: int, ids_pt
     sz = (ctypes.c_int * 3)(*size)
     _check(load().vl_get_blocks_window(grid, o, sz, capacity, off_ptr, ids_ptr, vals_ptr, on_device),
            "vl_get_blocks_window", grid)
+
+
+def vl_set_blocks_planes(grid, z0: int, nplanes: int, nblocks: int, off_ptr: int, ids_ptr: int,
+                         vals_ptr: int, on_device: int):
+    _check(load().vl_set_blocks_planes(grid, int(z0), int(nplanes), int(nblocks), off_ptr, ids_ptr,
+                                       vals_ptr, on_device), "vl_set_blocks_planes", grid)
 
 
 def vl_translate(grid, dt: float, order: str, nsteps: int, opts: vl_translate_opts | None):
