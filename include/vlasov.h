@@ -56,16 +56,17 @@ typedef enum {
 
 /* Storage of f in device memory (the paper fixes none; the arithmetic of a sweep is
  * float32 in every form).  The 16-bit forms keep q = f / s rounded to nearest even,
- * with one power-of-two float32 scale s per block id: s is the smallest power of two
- * >= the largest |f| of that block id in the state the step starts from (the limited
- * scheme creates no new maximum, so codes stay near or below 1).  Every value read
- * through this interface is float32 (q * s); every value written is rounded to the
- * storage type.  The fused form rounds once per step, the 3-pass form after each of
- * its three sweeps. */
+ * with one power-of-two float32 scale s per chunk -- the 16 values of one vz plane of a
+ * 4x4x4 block in one cell: whoever writes a chunk sets s to the smallest power of two
+ * >= its largest |f| (at least 2^-126, at most 2^127, 1 for an all-zero chunk), so
+ * every code lies in [-1, 1].  Every value read through this interface is float32
+ * (q * s); every value written is rounded to the storage type.  The fused form rounds
+ * once per step, the 3-pass form after each of its three sweeps.  The scales take 4
+ * bytes per 32 bytes of codes. */
 typedef enum {
     VL_STORE_F32 = 0,          /* f stored as float32 */
-    VL_STORE_BF16_SCALED = 1,  /* bfloat16 code x power-of-two float32 scale per block id */
-    VL_STORE_F16_SCALED = 2    /* float16 code x power-of-two float32 scale per block id */
+    VL_STORE_BF16_SCALED = 1,  /* bfloat16 code x power-of-two float32 scale per chunk */
+    VL_STORE_F16_SCALED = 2    /* float16 code x power-of-two float32 scale per chunk */
 } vl_storage;
 
 typedef enum {
@@ -197,8 +198,8 @@ vl_status vl_grid_destroy(vl_grid* grid);
  * NVLink-C2C on a Grace host, else it is staged through device buffers); 1: device
  * pointers on the grid's device (read on its stream before the call returns).
  * nblocks = cell_offsets[ncells].  values are float32; with
- * 16-bit storage they are rounded to it after the scale of each block id is taken from
- * their largest magnitude (host values then cross to the device twice).
+ * 16-bit storage each chunk of 16 is rounded to it with the scale of its own largest
+ * magnitude.
  * Errors: VL_EINVAL (offsets not non-decreasing, ids out of range or not strictly
  * increasing within a cell), VL_ENOMEM, VL_ECUDA. */
 vl_status vl_set_blocks(vl_grid* grid, int64_t nblocks, const int64_t* cell_offsets,
@@ -220,11 +221,11 @@ vl_status vl_get_blocks(vl_grid* grid, int64_t capacity, int64_t* cell_offsets,
  * the neighbours' boundary planes, which vl_get_blocks_window reads).  The lists cover
  * nx*ny*nplanes cells in window order (x fastest, then y, then the planes in order),
  * nblocks = cell_offsets[nx*ny*nplanes]; on_device as in vl_set_blocks.  When the
- * lists hold exactly the blocks the window already holds (with FP32 storage), their
- * values are written into the existing slots (work of the order of the window);
- * otherwise the layout is rebuilt from the whole state's lists on the device (work and
- * scratch memory of the order of the state; with 16-bit storage the codes are rounded
- * again with the scales of the new state).  Errors: VL_ESTATE (no state), VL_EINVAL, VL_ENOMEM, VL_ECUDA. */
+ * lists hold exactly the blocks the window already holds, their values are written into
+ * the existing slots (work of the order of the window); otherwise the layout is rebuilt
+ * from the whole state's lists on the device (work and scratch memory of the order of
+ * the state; 16-bit codes of the other cells come back unchanged, since re-deriving a
+ * chunk's scale from its decoded values reproduces its codes).  Errors: VL_ESTATE (no state), VL_EINVAL, VL_ENOMEM, VL_ECUDA. */
 vl_status vl_set_blocks_planes(vl_grid* grid, int z0, int nplanes, int64_t nblocks,
                                const int64_t* cell_offsets, const uint16_t* block_ids,
                                const float* values, int on_device);
@@ -248,11 +249,12 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                        const vl_translate_opts* opts);
 
 /* Checkpoint (the paper restarts its runs from a saved state, Section 4.2): the grid's
- * state as one self-describing host buffer -- a header (magic "VLGT", format version 2,
+ * state as one self-describing host buffer -- a header (magic "VLGT", format version 3,
  * spatial extents, velocity mesh, cell and velocity sizes, threshold, block count,
  * storage type, block ids) followed by the per-cell lists (cell_offsets, values,
- * block_ids) of vl_get_blocks and the per-block-id scales and maxima of 16-bit storage,
- * so that a restarted run continues bit for bit.
+ * block_ids) of vl_get_blocks.  A restarted run continues bit for bit: with 16-bit
+ * storage the decoded values determine the codes and scales (a chunk's scale re-derived
+ * from its decoded values reproduces its codes exactly).
  * vl_export with buf == NULL stores the required size in *size; otherwise *size must
  * hold the buffer's size (VL_ECAPACITY when too small) and receives the bytes written.
  * vl_import replaces the state of a grid with the same extents, velocity mesh and

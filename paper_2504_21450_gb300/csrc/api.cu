@@ -132,7 +132,6 @@ vl_status enqueue_step(Grid* g, StepArgs a, bool fused, bool graph, int64_t capa
         NvtxRange range("union + index");
         cudaMemsetAsync(ctr, 0, sizeof(StepCounters), g->stream);
         launch_union(g, A, B);
-        launch_out_scale(g, A, B);
         if (graph) {
             launch_index(g, B);
             launch_capacity_check(g, B, capacity, ctr);
@@ -685,8 +684,8 @@ struct CheckpointHeader {
     double vmin[3], dv[3], dx[3];
     double threshold;
     int64_t nblocks;
-    int32_t storage;  // version 2: vl_storage of the values' scales below
-    int32_t nb;       // version 2: block ids (length of the scale and vmax arrays)
+    int32_t storage;  // vl_storage of the grid the checkpoint came from
+    int32_t nb;       // block ids of the velocity mesh
 };
 }  // namespace
 
@@ -700,8 +699,7 @@ vl_status vl_export(vl_grid* grid, void* buf, size_t* size)
     if (st != VL_OK) return st;
     const int64_t N = g->geom.N;
     const int nb = g->geom.nb;
-    const size_t need = sizeof(CheckpointHeader) + (size_t)(N + 1) * 8 + (size_t)M * 2 + (size_t)M * 256 +
-                        (size_t)nb * 8 + 8;
+    const size_t need = sizeof(CheckpointHeader) + (size_t)(N + 1) * 8 + (size_t)M * 2 + (size_t)M * 256;
     if (!buf) {
         *size = need;
         return VL_OK;
@@ -710,7 +708,7 @@ vl_status vl_export(vl_grid* grid, void* buf, size_t* size)
                                                      " bytes, " + std::to_string(need) + " needed");
     CheckpointHeader h;
     std::memcpy(h.magic, "VLGT", 4);
-    h.version = 2;
+    h.version = 3;
     h.storage = (int32_t)g->storage;
     h.nb = nb;
     for (int d = 0; d < 3; d++) {
@@ -731,15 +729,11 @@ vl_status vl_export(vl_grid* grid, void* buf, size_t* size)
     p += (size_t)M * 256;
     uint16_t* ids = reinterpret_cast<uint16_t*>(p);
     p += (size_t)M * 2;
+    // 16-bit storage needs no scales in the checkpoint: a decoded value is q s with |q| <= 1,
+    // so the scale that importing derives from a chunk's decoded values is s / 2^k (k >= 0)
+    // and the new code q 2^k is exact; the state, and every later step, is the same
     st = get_blocks(g, M, off, ids, vals, 0);
     if (st != VL_OK) return st;
-    // scales of the 16-bit codes and the per-block-id maxima that set the next step's
-    // scales: restoring both makes a restarted run continue bit for bit
-    const Layout& L = g->lay[g->cur];
-    cudaMemcpyAsync(p, L.scale, (size_t)nb * 4, cudaMemcpyDeviceToHost, g->stream);
-    cudaMemcpyAsync(p + (size_t)nb * 4, L.vmax, (size_t)nb * 4, cudaMemcpyDeviceToHost, g->stream);
-    cudaError_t e = cudaStreamSynchronize(g->stream);
-    if (e != cudaSuccess) return cuda_fail(g, e, "vl_export");
     *size = need;
     return VL_OK;
 }
@@ -752,7 +746,7 @@ vl_status vl_import(vl_grid* grid, const void* buf, size_t size)
     CheckpointHeader h;
     if (size < sizeof(h)) return fail(g, VL_EINVAL, "vl_import: buffer too small");
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "VLGT", 4) != 0 || h.version != 2)
+    if (std::memcmp(h.magic, "VLGT", 4) != 0 || h.version != 3)
         return fail(g, VL_EINVAL, "vl_import: not a checkpoint of this library");
     if (h.storage != (int32_t)g->storage || h.nb != g->geom.nb)
         return fail(g, VL_EINVAL, "vl_import: storage type of the checkpoint differs from the grid's");
@@ -761,7 +755,7 @@ vl_status vl_import(vl_grid* grid, const void* buf, size_t size)
             h.dv[d] != g->vmesh.dv[d])
             return fail(g, VL_EINVAL, "vl_import: grid extents or velocity mesh differ");
     const int64_t N = g->geom.N, M = h.nblocks;
-    if (M < 0 || size < sizeof(h) + (size_t)(N + 1) * 8 + (size_t)M * 258 + (size_t)h.nb * 8)
+    if (M < 0 || size < sizeof(h) + (size_t)(N + 1) * 8 + (size_t)M * 258)
         return fail(g, VL_EINVAL, "vl_import: truncated checkpoint");
     const char* p = static_cast<const char*>(buf) + sizeof(h);
     const int64_t* off = reinterpret_cast<const int64_t*>(p);
@@ -769,12 +763,7 @@ vl_status vl_import(vl_grid* grid, const void* buf, size_t size)
     const float* vals = reinterpret_cast<const float*>(p);
     p += (size_t)M * 256;
     const uint16_t* ids = reinterpret_cast<const uint16_t*>(p);
-    p += (size_t)M * 2;
-    std::vector<float> scale((size_t)h.nb);
-    std::vector<unsigned> vmax((size_t)h.nb);
-    std::memcpy(scale.data(), p, (size_t)h.nb * 4);
-    std::memcpy(vmax.data(), p + (size_t)h.nb * 4, (size_t)h.nb * 4);
-    vl_status st = set_blocks(g, M, off, ids, vals, 0, scale.data(), vmax.data());
+    vl_status st = set_blocks(g, M, off, ids, vals, 0);
     if (st == VL_OK) {
         g->stats.mass = NAN;
         g->present = M;

@@ -16,8 +16,8 @@
 //     chunks per q, which keeps the 16-byte vector loads of a tile row coalesced.
 //   * dense[b]: bit 0 = every cell has a slot for b (rank = cell index), bit 1 = every
 //     cell holds b (kbits all set); sweeps skip the bitmaps when both are set.
-//   * Values are float32, or bfloat16 / float16 codes q of f = q * scale[b] with one
-//     power-of-two scale per block id (see Codec).
+//   * Values are float32, or bfloat16 / float16 codes q of f = q * scale[c] with one
+//     power-of-two scale per chunk c (c = float offset / 16; see Codec).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -37,17 +37,17 @@ struct LayoutView {
     const int64_t* base;
     const uint8_t* dense;
     void* pool;       // values in the grid's storage type (Codec<k>::T)
-    float* scale;     // [nb] power-of-two scale of the codes of block id b (16-bit storage)
-    unsigned* vmax;   // [nb] max |f| of block id b written so far (float bits), or nullptr
+    float* scale;     // [capacity * 4] power-of-two scale of the codes of each chunk
+                      // (16-bit storage; indexed like the chunks of the pool)
 };
 
 // Storage codecs.  FP32 storage keeps f.  The 16-bit forms keep q = f / s rounded to
-// nearest even in bfloat16 or float16, with s a power of two per block id: dividing
-// and multiplying by s is exact in FP32, so the rounding to 16 bits is the only error,
-// and the arithmetic of a sweep stays FP32.  s is at least the largest |f| of the block
-// id (see pow2_at_least), which keeps float16 codes of small values in its normal
-// range; codes a little above 1 (rounding, overshoot without the limiter) are still
-// representable in both formats.
+// nearest even in bfloat16 or float16, with s the power of two of the chunk (16 values,
+// one vz plane of a block) that q belongs to: dividing and multiplying by s is exact in
+// FP32, so the rounding to 16 bits is the only error, and the arithmetic of a sweep stays
+// FP32.  Whoever writes a chunk sets s from the largest |f| of the chunk (chunk_scale),
+// so every code lies in [-1, 1] and float16 codes of a chunk of small values stay in its
+// normal range however large the values elsewhere are.
 template <int kCodec>
 struct Codec;
 template <>
@@ -69,22 +69,30 @@ struct Codec<2> {
     static __device__ __forceinline__ T enc(float f, float inv) { return __float2half_rn(f * inv); }
 };
 
-// Smallest power of two >= m (m >= 0), from the FP32 bit fields; 1 for m = 0, at least
-// the smallest normal number, at most 2^127.
-__host__ __device__ inline float pow2_at_least(float m)
+// The scale of a chunk whose largest magnitude is m, and its inverse: s is the smallest
+// power of two >= m, clamped to [2^-126, 2^126] (2^-126 for an all-zero chunk), so both s
+// and 1/s are normal floats and encoding (f * inv) and decoding (q * s) are exact
+// scalings.  From the bit fields: adding 2^23 - 1 to the bits of a normal m carries into
+// the exponent exactly when its fraction is non-zero, and clearing the fraction then
+// leaves the next power of two up; s = 2^(e-127) has the inverse 2^(127-e), whose bits
+// are 0x7f000000 minus those of s.
+struct ChunkScale {
+    float s, inv;
+};
+__device__ __forceinline__ ChunkScale chunk_scale(float m)
 {
-    if (!(m > 0.0f)) return 1.0f;
-    union {
-        float f;
-        unsigned u;
-    } b;
-    b.f = m;
-    unsigned e = b.u >> 23;
-    if (e == 0) e = 1;                           // subnormal: 2^-126 covers it
-    else if ((b.u & 0x7fffffu) != 0) e += 1;     // not a power of two: next one up
-    if (e > 254) e = 254;
-    b.u = e << 23;
-    return b.f;
+    const float mc = fminf(fmaxf(m, 0x1p-126f), 0x1p126f);
+    const unsigned sb = (__float_as_uint(mc) + 0x007fffffu) & 0x7f800000u;
+    return ChunkScale{__uint_as_float(sb), __uint_as_float(0x7f000000u - sb)};
+}
+// Largest value over aligned groups of `width` lanes (a power of two <= 32); every lane
+// of the warp must take part.
+template <int width>
+__device__ __forceinline__ float group_max(float m)
+{
+#pragma unroll
+    for (int o = width / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
 }
 
 struct GridGeom {

@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(256) k_cell_moments(GridGeom G, LayoutView L, 
         const int64_t base = L.base[b];
         const int64_t cnt = L.cnt[b];
         const bool dense = (L.dense[b] & 1) != 0;
-        const float sc = kCodec ? L.scale[b] : 1.0f;
         const int bc[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
         double vb[3];
         for (int d = 0; d < 3; d++) vb[d] = V.vmin[d] + (4 * bc[d] + 2) * V.dv[d];
@@ -86,7 +85,9 @@ __global__ void __launch_bounds__(256) k_cell_moments(GridGeom G, LayoutView L, 
             float a = 0.f, e[3] = {0.f, 0.f, 0.f}, q[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int iz = 0; iz < 4; iz++) {
-                const T* src = pool + (base * 4 + iz * cnt + rank) * kChunk;
+                const int64_t chunk = base * 4 + iz * cnt + rank;
+                const T* src = pool + chunk * kChunk;
+                const float sc = kCodec ? L.scale[chunk] : 1.0f;
                 const float dz = (iz - 1.5f) * dvz;
 #pragma unroll
                 for (int l = 0; l < kChunk; l++) {

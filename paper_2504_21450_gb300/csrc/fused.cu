@@ -54,7 +54,10 @@ struct Shape {
     static constexpr int STAGE = EY * SROW;
     static constexpr int XBUF = EY * XROW;
     static constexpr int TABS = 2 * EX + 2 * EY;
-    static constexpr int SMEM = NST * STAGE * ES + 2 * XBUF * 4 + TABS * 4 + 4 * TX * TY * 4 + 3 * 16 * 4 + 64;
+    // 16-bit storage adds the chunk scales of the staged cells ([NST][EY][EX] floats)
+    static constexpr int SCALES = ES < 4 ? NST * EY * EX : 0;
+    static constexpr int SMEM = NST * STAGE * ES + 2 * XBUF * 4 + TABS * 4 + 4 * TX * TY * 4 + 3 * 16 * 4 +
+                                SCALES * 4 + 64;
     static_assert(NX < NT, "sweep-0 rows must leave threads to stage planes");
     static_assert(NH * TX * NV == NT && NH * L == TY, "sweep-1 segments must tile the CTA");
 };
@@ -83,6 +86,13 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
 {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+// 4-byte copy global -> shared (the chunk scale of a staged cell); src_bytes = 0 writes 0
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem), "r"(src_bytes)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -173,6 +183,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
     int* pr1 = px1 + EY;
     int* orank = pr1 + EY;                                           // [4][TY][TX]
     unsigned* kb = reinterpret_cast<unsigned*>(orank + 4 * TX * TY);  // [3][16 warps]
+    float* isc = reinterpret_cast<float*>(kb + 3 * 16);               // [NST][EY][EX] (16-bit)
     __shared__ int64_t s_work;
     __shared__ __align__(8) uint64_t s_bar[NST];  // staging barriers of the bulk copies
     __shared__ int s_run[EX][3];                  // contiguous runs of a halo row: u0, x, len
@@ -244,10 +255,6 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         const int64_t okeep = (int64_t)P.out.base[b];
         const T* ipool = static_cast<const T*>(P.in.pool);
         T* opool = static_cast<T*>(P.out.pool);
-        // 16-bit storage: scales of the codes read and written (powers of two)
-        const float sc_in = kCodec ? P.in.scale[b] : 1.0f;
-        const float sc_out = kCodec ? P.out.scale[b] : 1.0f;
-        const float inv_out = 1.0f / sc_out;
 
         // contiguous runs of a halo row along axis 0 (split at the periodic wrap)
         if (tid == 0 && (bulk || sbulk)) {
@@ -385,6 +392,18 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                         cp_async16(st + u1 * SROW + u0 * NV + PE * piece, src, r >= 0 ? 16 : 0);
                     }
                 }
+                if constexpr (kCodec != 0) {
+                    // chunk scales of the staged cells, one 4-byte copy each (0 for an absent
+                    // cell, whose codes are zero), in this plane's cp.async group
+                    float* sc = isc + (s % NST) * EY * EX;
+                    for (int c = ltid; c < EX * EY; c += NLD) {
+                        const int u1 = c / EX, u0 = c - u1 * EX;
+                        const int x = px0[u0] + px1[u1] + x2;
+                        const int64_t row = (int64_t)pr0[u0] + pr1[u1] + r2;
+                        const int64_t r = dense_in ? row * G.n[0] + x : cell_rank(P.in, G, b, x, row, true);
+                        cp_async4(sc + c, r >= 0 ? P.in.scale + ibase / NV + r : P.in.scale, r >= 0 ? 4 : 0);
+                    }
+                }
             }
             cp_async_commit();
         };
@@ -475,11 +494,17 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
 #pragma unroll
         for (int j = 0; j < (kZUni ? 1 : L); j++) zg[j].reset();
         float msum = 0.0f, mcomp = 0.0f;  // Kahan-compensated FP32 mass of this thread
-        float vmx = 0.0f;                 // largest |stored value| (16-bit storage)
 
         if (loader) {
             issue_plane(0);
             issue_plane(1);
+        }
+        // 16-bit storage with bulk-staged planes: the scales of a plane come by cp.async,
+        // which the staging barrier does not cover.  Plane 0's are waited for here; from
+        // then on the loaders wait for plane s+1's in step s, before its second barrier.
+        if (kCodec != 0 && (bulk || sbulk)) {
+            if (loader) cp_async_wait<NST - 2>();
+            __syncthreads();
         }
 
         // one streamed plane; kEmit: the plane completes an output plane
@@ -496,19 +521,20 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             if (!loader) {
                 // sweep 0 along axis 0 on halo row `hi`
                 const T* line = stage + (s % NST) * S::STAGE + hi * SROW + v;
+                const float* lsc = isc + (s % NST) * EY * EX + hi * EX;  // 16-bit: chunk scales
                 float* xo = xbuf + (s & 1) * S::XBUF + hi * XROW + v;
                 Walk<kLim> wk;
                 wk.reset();
                 if (kw[0].up) {
 #pragma unroll
                     for (int t = 0; t < TX + 5; t++) {
-                        float r = wk.push(C::dec(line[t * NV], sc_in), kx);
+                        float r = wk.push(C::dec(line[t * NV], kCodec ? lsc[t] : 1.0f), kx);
                         if (t >= 5) xo[(t - 5) * NV] = r;
                     }
                 } else {
 #pragma unroll
                     for (int t = 0; t < TX + 5; t++) {
-                        float r = wk.push(C::dec(line[(TX + 5 - t) * NV], sc_in), kx);
+                        float r = wk.push(C::dec(line[(TX + 5 - t) * NV], kCodec ? lsc[TX + 5 - t] : 1.0f), kx);
                         if (t >= 5) xo[(TX + 4 - t) * NV] = r;
                     }
                 }
@@ -516,6 +542,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                 keep_flags(s - 2);
                 out_ranks(s + 1);
                 issue_plane(s + NST - 1);
+                if (kCodec != 0 && (bulk || sbulk)) cp_async_wait<NST - 2>();  // plane s+1's scales
             }
             __syncthreads();  // sweep-0 rows complete
             // a staging wait of this plane ran out: no sweep on an incomplete plane.  The
@@ -533,15 +560,26 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
             const int* orow = orank + (s & 3) * TX * TY + j0 * TX + ci;
             float psum = 0.0f;
             unsigned kmask = 0;
-            auto emit = [&](int jj, float res) {
+            // new value of row jj.  16-bit storage: the 16 lanes of a half warp hold the 16
+            // values of one chunk of one cell, and lane groups that walk sweep 1 in
+            // opposite directions (a block straddling v = 0 along axis 1) produce the
+            // rows in opposite orders, so the rows are collected first and stored after
+            // the walk, by every lane together
+            auto store_row = [&](int jj, float res) {
                 if (kEmit) {
-                    const T code = C::enc(res, inv_out);
-                    if (kCodec) {
-                        res = C::dec(code, sc_out);  // the value the state now holds
-                        vmx = fmaxf(vmx, fabsf(res));
+                    T code;
+                    float sco = 1.0f;  // 16-bit storage: the chunk's new scale
+                    if constexpr (kCodec != 0) {
+                        const ChunkScale cs = chunk_scale(group_max<16>(fabsf(res)));
+                        code = C::enc(res, cs.inv);
+                        res = C::dec(code, cs.s);  // the value the state now holds
+                        sco = cs.s;
+                    } else {
+                        code = res;
                     }
                     if (fast) {
                         dst[jj * dstep] = code;
+                        if (kCodec != 0 && v == 0) P.out.scale[((dst - opool) + jj * dstep) >> 4] = sco;
                         psum += res;
                     } else {
                         int64_t r = -1;
@@ -551,13 +589,21 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                             r = orow[jj * TX];
                         }
                         if (r >= 0) {
-                            if (dense_out) dst[jj * dstep] = code;
-                            else opool[obase + r * NV + v] = code;
+                            int64_t e;  // element offset of the value in the output pool
+                            if (dense_out) e = (dst - opool) + jj * dstep;
+                            else e = obase + r * NV + v;
+                            opool[e] = code;
+                            if (kCodec != 0 && v == 0) P.out.scale[e >> 4] = sco;
                             psum += res;
                         }
                     }
                     if (res >= P.thr) kmask |= 1u << jj;
                 }
+            };
+            float rows[kCodec ? L : 1];
+            auto emit = [&](int jj, float res) {
+                if constexpr (kCodec != 0) rows[jj] = res;
+                else store_row(jj, res);
             };
             // sweep-1 output of row jj into its streamed window; rows are produced in
             // walking order (ascending when kUp), and a packed pair is pushed once both
@@ -598,6 +644,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
                     float r = wk.push(line[(L + 5 - t) * XROW], kw[1]);
                     if (t >= 5) consume(L + 4 - t, r, std::false_type{});
                 }
+            }
+            if constexpr (kCodec != 0) {
+#pragma unroll
+                for (int jj = 0; jj < L; jj++) store_row(jj, rows[jj]);
             }
             if (kEmit) {
                 unsigned km = __reduce_or_sync(0xffffffffu, kmask << (16 * (ci & 1)));
@@ -644,10 +694,6 @@ __global__ void __launch_bounds__(NT, 1) k_fused(FusedArgs P)
         double m = (double)msum;
         for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
         if (lane == 0 && m != 0.0) atomicAdd(&P.ctr->mass, m);
-        if (kCodec) {
-            unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
-            if (lane == 0 && u) atomicMax(&P.out.vmax[b], u);
-        }
     }
     if (P.cta_done && tid == 0) P.cta_done[blockIdx.x] = globaltimer_ns();
 }

@@ -27,13 +27,12 @@ struct Layout {
     uint8_t* dense = nullptr;    // [nb]
     uint32_t* kcnt = nullptr;    // [nb] kept blocks per id
     void* pool = nullptr;        // [capacity * 64] values in the storage type
-    float* scale = nullptr;      // [nb] power-of-two scale of the 16-bit codes
-    unsigned* vmax = nullptr;    // [nb] max |f| per block id (float bits)
+    float* scale = nullptr;      // [capacity * 4] power-of-two scale per chunk (16-bit storage)
     uint8_t* keepq = nullptr;    // [capacity * 4] per-chunk keep flags of the last sweep
     int64_t capacity = 0;        // blocks the pool can hold
     int64_t total = 0;           // slots in use (host copy)
 
-    LayoutView view() const { return LayoutView{ubits, kbits, woff, cnt, base, dense, pool, scale, vmax}; }
+    LayoutView view() const { return LayoutView{ubits, kbits, woff, cnt, base, dense, pool, scale}; }
 };
 
 struct Grid {
@@ -103,9 +102,6 @@ void layout_free(Grid* g, Layout& L);
 vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks);
 // Frees a layout's value pool and keep flags (its bitmaps stay).
 void layout_release_pool(Grid* g, Layout& L);
-// 16-bit storage: scale of the next layout's codes from the current layout's largest
-// values (translation with the limiter creates no new maximum), and its vmax cleared.
-void launch_out_scale(Grid* g, const Layout& cur, Layout& next);
 // Like layout_ensure_pool, but keeps the L.total blocks the pool holds.
 vl_status layout_grow_pool(Grid* g, Layout& L, int64_t blocks);
 // Counts, offsets and dense flags of L from its ubits (woff, cnt, base, dense);
@@ -120,11 +116,8 @@ void launch_index(Grid* g, Layout& L);
 void launch_pack_keep(Grid* g, Layout& next, StepCounters* ctr);
 // Sets the abort flag and ctr->error bit 3 when L's slot total exceeds capacity.
 void launch_capacity_check(Grid* g, const Layout& L, int64_t capacity, StepCounters* ctr);
-// scale_host / vmax_host (host, nb each, optional): codes of 16-bit storage use these
-// scales instead of ones derived from the values, and the maxima are restored (import).
 vl_status set_blocks(Grid* g, int64_t nblocks, const int64_t* off, const uint16_t* ids,
-                     const float* vals, int on_device, const float* scale_host = nullptr,
-                     const unsigned* vmax_host = nullptr);
+                     const float* vals, int on_device);
 vl_status get_block_count(Grid* g, int64_t* n);
 // Replaces the blocks of z-planes z0 .. z0+nplanes-1 (wrapping) by the given lists (in
 // window order) and keeps every other cell.

@@ -43,6 +43,10 @@ constexpr int kNX = kNB * kLines * 8;       // sweep-0 walks per batch (lane pai
 constexpr int kNY = kNB * kT * 8;           // sweep-1 walks per batch
 constexpr int kNS = kNC - kNY;              // staging threads: those that sit out sweep 1
 constexpr int kFirst = kHalo + 2;           // first streamed plane that completes an output
+// 16-bit storage with sweep 0 along x: the codes of a staged row are packed (8 floats per
+// cell) at the end of the row that sweep 0 reaches last -- from float kCodesHi when it
+// walks up, from float 0 when it walks down
+constexpr int kCodesHi = kRP - kE * kChunk / 2;
 static_assert(kNX <= kNC && kNY <= kNC, "walks of a batch must fit the compute threads");
 static_assert(kT * kT * 4 == 2 * kNC, "sweep 2: two tile cells x one vx row per thread");
 static_assert(kNS == 128, "staging threads: warps 12-15 (named barrier 1)");
@@ -61,7 +65,13 @@ struct Gt3Smem {
     int pref;                 // batch 0 of the current item was staged during the last one
     int abort;
 };
-constexpr size_t kSmem = sizeof(Gt3Smem);
+// 16-bit storage: the chunk scales of the staged cells, [2][kNB][kE * kE] floats after
+// Gt3Smem (per batch buffer and plane, staged row-major like the cells)
+constexpr int kScales = 2 * kNB * kE * kE;
+template <int kCodec>
+constexpr size_t smem_bytes() { return sizeof(Gt3Smem) + (kCodec ? kScales * sizeof(float) : 0); }
+__device__ __forceinline__ float* scales_of(Gt3Smem& S) { return reinterpret_cast<float*>(&S + 1); }
+static_assert(smem_bytes<1>() <= 227 * 1024, "shared memory of one CTA");
 
 struct Gt3Args {
     GridGeom G;
@@ -143,13 +153,19 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
 }
+// 4-byte copy global -> shared; src_bytes = 0 writes 0
+__device__ __forceinline__ void cp4(void* dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(su32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 // the barrier's pending count drops by one once this thread's earlier cp.async copies land
 __device__ __forceinline__ void cp_arrive(uint64_t* bar)
 {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(su32(bar)) : "memory");
 }
 
-// Two 16-bit codes (lanes l, l+1) as floats times the block id's scale, as Codec::dec
+// Two 16-bit codes (lanes l, l+1) as floats times their chunk's scale, as Codec::dec
 // does per value (the scale is a power of two: exact).
 template <int kCodec>
 __device__ __forceinline__ float2 dec2(uint32_t w, float2 s)
@@ -199,7 +215,7 @@ __device__ __forceinline__ int rowpart(int d, int c, int ny) { return d == 1 ? c
 // One work item: block id b, velocity chunk q, tile origin and extent.
 struct Item {
     int b, q, tx0, tr0, ex, er;
-    bool dense_in, dense_out, up2;
+    bool dense_in, dense_out, up0, up2;
     int64_t ibase, obase;
 };
 
@@ -231,6 +247,10 @@ __device__ __forceinline__ Item decode_item(const Gt3Args& P, int64_t w)
     const int d = P.ax[2];
     const int bc = d == 1 ? (lo / G.nbx) % G.nby : lo / (G.nbx * G.nby);
     it.up2 = P.walk[d * P.nvmax + bc * 4 + (d == 2 ? it.q : 0)].w != 0.0f;
+    // and along the axis of sweep 0 (uniform for the same reason)
+    const int d0 = P.ax[0];
+    const int bc0 = d0 == 0 ? lo % G.nbx : (d0 == 1 ? (lo / G.nbx) % G.nby : lo / (G.nbx * G.nby));
+    it.up0 = P.walk[d0 * P.nvmax + bc0 * 4 + (d0 == 2 ? it.q : 0)].w != 0.0f;
     return it;
 }
 
@@ -260,12 +280,16 @@ __device__ __forceinline__ void item_tables(const Gt3Args& P, Gt3Smem& S, const 
 
 // Staging of batch k of an item (planes kNB k .. kNB k + 2 of its stream) into buffer
 // g & 1, g = the CTA's running batch index; run by the kNS staging threads (sl = 0..127).
-// FP32 storage: TMA bulk copies of contiguous runs.  16-bit storage: the 32 bytes of
-// codes of each staged cell go to the upper half of its 64-byte slot with two 16-byte
-// cp.async copies (sweep 0 decodes them and writes its FP32 result into the slot of the
-// cell two positions behind, whose codes it has already read), and every staging
-// thread arrives on the barrier once its copies have landed.
-template <int kCodec>
+// FP32 storage: TMA bulk copies of contiguous runs.  16-bit storage: one staging thread
+// per staged row, and every staging thread arrives on the barrier once its copies have
+// landed.  The chunk scale of each staged cell goes into the scale table with a 4-byte
+// cp.async copy (0 for an absent cell).  With sweep 0 along x the row's codes are packed
+// at one end of the row (kCodesHi) by bulk copies per contiguous run: sweep 0 walks
+// towards that end and writes its FP32 result two cells behind the one it reads, which
+// overwrites only codes read at least three positions earlier.  Otherwise the 32 bytes of
+// codes of each cell go to the upper half of its own 64-byte slot with two 16-byte
+// cp.async copies, so that each line of sweep 0 overwrites only codes it has read.
+template <int kCodec, bool kA0X>
 __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const Item& it, int t, int k,
                                             unsigned g, int sl)
 {
@@ -281,26 +305,87 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
     auto out_of = [&](int s) { return it.up2 ? s - kFirst : n2 + 4 - s; };
     if constexpr (kCodec != 0) {
         using T = typename Codec<kCodec>::T;
-        const T* cpool = static_cast<const T*>(P.in.pool);
-        const int npiece = nj * kE * kE * 2;
-        for (int i = sl; i < npiece; i += kNS) {
-            const int piece = i & 1, c = i >> 1;
-            const int u = c % kE, rr = c / kE;
-            const int rho = rr % kE, j = rr / kE;
-            const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, wrapi(plane_of(kNB * k + j), n2), ny);
-            const int x = S.xs[t][u];
-            int64_t r;
-            if (it.dense_in) {
-                r = row * nx + x;
+        const T* cpool = static_cast<const T*>(P.in.pool) + it.ibase;  // codes of rank 0
+        const float* spool = P.in.scale + it.ibase / kChunk;            // scale of rank 0
+        if (sl < nj * kE) {
+            const int j = sl / kE, rho = sl - j * kE;
+            const int pz = wrapi(plane_of(kNB * k + j), n2);
+            const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
+            float* drow = &S.buf[slot][j][rho * kRP];
+            float* srow = scales_of(S) + ((slot * kNB + j) * kE + rho) * kE;
+            if constexpr (kA0X) {
+                float* codes = drow + (it.up0 ? kCodesHi : 0);
+                fence_async_smem();
+                if (it.dense_in) {
+                    const int64_t r0 = row * nx;
+                    for (int k2 = 0; k2 < nrun; k2++)
+                        copy_g2s(codes + S.run[t][k2][0] * (kChunk / 2), cpool + (r0 + S.run[t][k2][1]) * kChunk,
+                                 (unsigned)(S.run[t][k2][2] * kChunk * sizeof(T)), bar);
+                    for (int u = 0; u < kE; u++) cp4(srow + u, spool + r0 + S.xs[t][u], 4);
+                } else {
+                    // runs of present cells (consecutive slots) as bulk copies, each announced
+                    // to the barrier before it is issued; absent cells get zero codes and scale
+                    const int64_t wbase = (int64_t)it.b * G.RW + row * G.W;
+                    for (int k2 = 0; k2 < nrun; k2++) {
+                        const int u0 = S.run[t][k2][0], x0 = S.run[t][k2][1], len = S.run[t][k2][2];
+                        const int w0 = x0 >> 6, sh = x0 & 63;
+                        const bool two = sh + len > 64;
+                        const uint64_t ua = P.in.ubits[wbase + w0];
+                        const uint64_t ub = two ? P.in.ubits[wbase + w0 + 1] : 0ull;
+                        const uint32_t oa = P.in.woff[wbase + w0];
+                        const uint32_t ob = two ? P.in.woff[wbase + w0 + 1] : 0u;
+                        const uint64_t lenmask = (1ull << len) - 1ull;  // len <= 22
+                        uint64_t pm = (P.in.kbits[wbase + w0] & ua) >> sh;
+                        if (two) pm |= (P.in.kbits[wbase + w0 + 1] & ub) << (64 - sh);
+                        pm &= lenmask;
+                        uint64_t absent = ~pm & lenmask;
+                        while (absent) {
+                            const int u = u0 + __ffsll((long long)absent) - 1;
+                            absent &= absent - 1ull;
+                            cp16(codes + u * (kChunk / 2), cpool, 0);
+                            cp16(codes + u * (kChunk / 2) + 4, cpool, 0);
+                            cp4(srow + u, spool, 0);
+                        }
+                        uint64_t m = pm;
+                        while (m) {
+                            const int u = __ffsll((long long)m) - 1;
+                            const int rl = __ffsll((long long)~(m >> u)) - 1;
+                            const int x = x0 + u;
+                            const bool lw = (x >> 6) == w0;
+                            const int64_t r = (int64_t)(lw ? oa : ob) + __popcll((lw ? ua : ub) & ((1ull << (x & 63)) - 1ull));
+                            const unsigned bytes = (unsigned)(rl * kChunk * sizeof(T));
+                            bar_add_tx(bar, bytes);
+                            copy_g2s(codes + (u0 + u) * (kChunk / 2), cpool + r * kChunk, bytes, bar);
+                            for (int i = 0; i < rl; i++) cp4(srow + u0 + u + i, spool + r + i, 4);
+                            m &= ~(((1ull << rl) - 1ull) << u);
+                        }
+                    }
+                }
             } else {
-                const int64_t wi = (int64_t)it.b * G.RW + row * G.W + (x >> 6);
-                const uint64_t bit = 1ull << (x & 63);
-                const uint64_t uw = P.in.ubits[wi];
-                r = ((uw & P.in.kbits[wi] & bit) != 0ull) ? (int64_t)P.in.woff[wi] + __popcll(uw & (bit - 1ull)) : -1;
+                for (int u = 0; u < kE; u++) {
+                    const int x = S.xs[t][u];
+                    int64_t r;
+                    if (it.dense_in) {
+                        r = row * nx + x;
+                    } else {
+                        const int64_t wi = (int64_t)it.b * G.RW + row * G.W + (x >> 6);
+                        const uint64_t bit = 1ull << (x & 63);
+                        const uint64_t uw = P.in.ubits[wi];
+                        r = ((uw & P.in.kbits[wi] & bit) != 0ull) ? (int64_t)P.in.woff[wi] + __popcll(uw & (bit - 1ull))
+                                                                   : -1;
+                    }
+                    float* dst = drow + u * kChunk + 8;
+                    const T* src = r >= 0 ? cpool + r * kChunk : cpool;
+                    const int nbytes = r >= 0 ? 16 : 0;
+                    cp16(dst, src, nbytes);
+                    cp16(dst + 4, src + 8, nbytes);
+                    cp4(srow + u, r >= 0 ? spool + r : spool, r >= 0 ? 4 : 0);
+                }
             }
-            float* dst = &S.buf[slot][j][rho * kRP + u * kChunk + 8 + 4 * piece];
-            cp16(dst, r >= 0 ? cpool + it.ibase + r * kChunk + 8 * piece : cpool, r >= 0 ? 16 : 0);
         }
+        // dense rows with sweep 0 along x: the batch's code bytes, announced without an
+        // arrival (the phase also waits for every staging thread's arrival below)
+        if (kA0X && it.dense_in && sl == 0) bar_add_tx(bar, (unsigned)(nj * kE * kE * kChunk * sizeof(T)));
         cp_arrive(bar);
     } else if (it.dense_in) {
         // one arrival carrying the batch's bytes; the copies of the other staging
@@ -413,6 +498,9 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
     // staged offsets of a position along sweep axis 0 / 1 (in floats)
     constexpr int kS0 = kA0X ? kChunk : kRP;
     constexpr int kS1 = kA0X ? kRP : kChunk;
+    // the same for the scale table (one float per staged cell)
+    constexpr int kC0 = kA0X ? 1 : kE;
+    constexpr int kC1 = kA0X ? kE : 1;
 
     if (tid == 0) {
         // FP32: one arrival (with the batch's bytes); 16-bit: one per staging thread
@@ -437,13 +525,6 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
         const int64_t okeep = (int64_t)P.out.base[it.b];
         using T = typename Codec<kCodec>::T;
         T* opool = static_cast<T*>(P.out.pool);
-        // 16-bit storage: scales of the codes read and written (powers of two)
-        const float sc_in = kCodec ? P.in.scale[it.b] : 1.0f;
-        const float sc_out = kCodec ? P.out.scale[it.b] : 1.0f;
-        const float2 sc_in2 = make_float2(sc_in, sc_in);
-        const float2 sc_out2 = make_float2(sc_out, sc_out);
-        const float2 inv_out2 = make_float2(1.0f / sc_out, 1.0f / sc_out);
-        float vmx = 0.0f;  // largest |stored value| of this item (16-bit storage)
         if (!pref) item_tables(P, S, it, ti, tid);
         if (tid < 3 * kChunk) {
             // sweep constants of the item's 16 velocity cells (v = vx + 4 vy, vz = q)
@@ -481,7 +562,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             kz.B = make_float2(c.z, c.z);
         }
 
-        if (stager && !pref) stage_batch<kCodec>(P, S, it, ti, 0, gb, sl);
+        if (stager && !pref) stage_batch<kCodec, kA0X>(P, S, it, ti, 0, gb, sl);
         int k = 0;
         for (; k < nbatch; k++) {
             const unsigned slot = (gb + k) & 1u;
@@ -501,11 +582,23 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                     const float4 c0 = S.kc[0][l0], c1 = S.kc[0][l0 + 1];
                     const WalkConst2 kx{make_float2(c0.x, c1.x), make_float2(c0.y, c1.y), make_float2(c0.z, c1.z)};
                     float* p = B + j * kPS + (line + (up1 ? 0 : 1)) * kS1 + l0;
+                    // 16-bit storage: chunk scales of the line's cells
+                    const float* ps = scales_of(S) + (slot * kNB + j) * kE * kE + (line + (up1 ? 0 : 1)) * kC1;
                     // the two staged values of position m: FP32, or two 16-bit codes in the
                     // upper half of the cell's slot
+                    // packed codes of the line (sweep 0 along x), see stage_batch
+                    const uint32_t* pc = reinterpret_cast<const uint32_t*>(
+                                             B + j * kPS + (line + (up1 ? 0 : 1)) * kRP + (up0 ? kCodesHi : 0)) +
+                                         (l0 >> 1);
                     auto in = [&](int m) -> float2 {
-                        if constexpr (kCodec == 0) return lds2(p + m * kS0);
-                        else return dec2<kCodec>(reinterpret_cast<const uint32_t*>(p - l0 + m * kS0)[8 + (l0 >> 1)], sc_in2);
+                        if constexpr (kCodec == 0) {
+                            return lds2(p + m * kS0);
+                        } else {
+                            const float sc = ps[m * kC0];
+                            const uint32_t w = kA0X ? pc[m * (kChunk / 2)]
+                                                    : reinterpret_cast<const uint32_t*>(p - l0 + m * kS0)[8 + (l0 >> 1)];
+                            return dec2<kCodec>(w, make_float2(sc, sc));
+                        }
                     };
                     Walk2<kLim> wk;
                     wk.reset();
@@ -528,7 +621,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             if (S.abort) break;
             if (stager) {
                 if (k + 1 < nbatch) {
-                    stage_batch<kCodec>(P, S, it, ti, k + 1, gb + k + 1, sl);
+                    stage_batch<kCodec, kA0X>(P, S, it, ti, k + 1, gb + k + 1, sl);
                 } else {
                     // last batch: stage the first batch of the next item
                     const int64_t wn = S.next;
@@ -536,7 +629,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                         const Item nx = decode_item(P, wn);
                         item_tables(P, S, nx, ti ^ 1, tid);
                         asm volatile("bar.sync 1, %0;\n" ::"n"(kNS) : "memory");
-                        stage_batch<kCodec>(P, S, nx, ti ^ 1, 0, gb + nbatch, sl);
+                        stage_batch<kCodec, kA0X>(P, S, nx, ti ^ 1, 0, gb + nbatch, sl);
                         if (sl == 0) S.pref = 1;
                     }
                 }
@@ -593,29 +686,39 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                 }
                 float psum = 0.0f;
                 bool keep0 = false, keep1 = false;
+                // 16-bit storage: the scale of each of the two cells' chunk, from the largest
+                // magnitude over the four threads (vx rows) of the cell
+                ChunkScale cs0{1.0f, 1.0f}, cs1{1.0f, 1.0f};
+                if constexpr (kCodec != 0) {
+                    cs0 = chunk_scale(group_max<4>(
+                        fmaxf(fmaxf(fabsf(r00.x), fabsf(r00.y)), fmaxf(fabsf(r01.x), fabsf(r01.y)))));
+                    cs1 = chunk_scale(group_max<4>(
+                        fmaxf(fmaxf(fabsf(r10.x), fabsf(r10.y)), fmaxf(fabsf(r11.x), fabsf(r11.y)))));
+                }
                 // store one vx row (4 values) of a cell; v0, v1 become the values the state
                 // now holds (16-bit storage: the codes decoded)
-                auto store = [&](int64_t rk, float2& v0, float2& v1) {
+                auto store = [&](int64_t rk, float2& v0, float2& v1, const ChunkScale& cs) {
                     T* dst = opool + it.obase + rk * kChunk + 4 * zq;
                     if constexpr (kCodec == 0) {
                         *reinterpret_cast<float4*>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
                     } else {
-                        const uint32_t w0 = enc2<kCodec>(v0, inv_out2), w1 = enc2<kCodec>(v1, inv_out2);
+                        const float2 inv = make_float2(cs.inv, cs.inv), sc = make_float2(cs.s, cs.s);
+                        const uint32_t w0 = enc2<kCodec>(v0, inv), w1 = enc2<kCodec>(v1, inv);
                         *reinterpret_cast<uint2*>(dst) = make_uint2(w0, w1);
-                        v0 = dec2<kCodec>(w0, sc_out2);
-                        v1 = dec2<kCodec>(w1, sc_out2);
-                        vmx = fmaxf(vmx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                        if (zq == 0) P.out.scale[it.obase / kChunk + rk] = cs.s;
+                        v0 = dec2<kCodec>(w0, sc);
+                        v1 = dec2<kCodec>(w1, sc);
                     }
                 };
                 if (rk0 >= 0) {
                     float2 v0 = r00, v1 = r01;
-                    store(rk0, v0, v1);
+                    store(rk0, v0, v1, cs0);
                     psum += (v0.x + v0.y) + (v1.x + v1.y);
                     keep0 = fmaxf(fmaxf(v0.x, v0.y), fmaxf(v1.x, v1.y)) >= P.thr;
                 }
                 if (rk1 >= 0) {
                     float2 v0 = r10, v1 = r11;
-                    store(rk1, v0, v1);
+                    store(rk1, v0, v1, cs1);
                     psum += (v0.x + v0.y) + (v1.x + v1.y);
                     keep1 = fmaxf(fmaxf(v0.x, v0.y), fmaxf(v1.x, v1.y)) >= P.thr;
                 }
@@ -644,10 +747,6 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             if (tid == 0 && k < nbatch) bar_wait_bounded(&S.bar[(gb + k) & 1u], ((gb + k) >> 1) & 1u);
             break;
         }
-        if (kCodec) {
-            const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
-            if (lane == 0 && u) atomicMax(&P.out.vmax[it.b], u);
-        }
         gb += (unsigned)nbatch;
     }
     double m = (double)msum;
@@ -661,13 +760,13 @@ template <bool kLim, bool kA0X, int kCodec>
 vl_status launch_gt3(Grid* g, const Gt3Args& P)
 {
     auto kern = k_gt3<kLim, kA0X, kCodec>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<kCodec>());
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
     Gt3Args Q = P;
     if (nsm > kMaxCtas) Q.cta_done = nullptr;
     g->cta_count = Q.cta_done ? nsm : 0;
-    kern<<<nsm, kNT, kSmem, g->stream>>>(Q);
+    kern<<<nsm, kNT, smem_bytes<kCodec>(), g->stream>>>(Q);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(g, e, "plane-batched fused sweep launch");

@@ -221,11 +221,12 @@ __global__ void k_pack_keep(GridGeom G, LayoutView L, const uint8_t* __restrict_
                 // values of one block: relative error ~1e-7 of a dropped block's mass);
                 // the chunk sums are accumulated in FP64
                 using T = typename Codec<kCodec>::T;
-                const float sc = kCodec ? L.scale[b] : 1.0f;
                 float cs[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const T* p = static_cast<const T*>(L.pool) + (bb * 4 + (int64_t)q * cb + rank) * kChunk;
+                    const int64_t ci = bb * 4 + (int64_t)q * cb + rank;  // chunk index
+                    const float sc = kCodec ? L.scale[ci] : 1.0f;
+                    const T* p = static_cast<const T*>(L.pool) + ci * kChunk;
                     float part[4] = {0.f, 0.f, 0.f, 0.f};
                     if constexpr (kCodec == 0) {
                         const float4* p4 = reinterpret_cast<const float4*>(p);
@@ -326,8 +327,18 @@ __global__ void k_scatter(GridGeom G, LayoutView L, const uint16_t* __restrict__
     int x = (int)(c % G.n[0]);
     int64_t rank = cell_rank(L, G, b, x, c / G.n[0], false);
     int64_t dst = ((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15);
-    static_cast<typename Codec<kCodec>::T*>(L.pool)[dst] =
-        Codec<kCodec>::enc(vals[i], kCodec ? 1.0f / L.scale[b] : 1.0f);
+    const float f = vals[i];
+    float inv = 1.0f;
+    if constexpr (kCodec != 0) {
+        // the 16 values of a chunk are 16 consecutive threads (a half warp, since every
+        // block's 64 values start at a warp boundary): their largest magnitude sets the
+        // chunk's power-of-two scale
+        const unsigned half = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+        const ChunkScale cs = chunk_scale(__uint_as_float(__reduce_max_sync(half, __float_as_uint(fabsf(f)))));
+        if ((v & 15) == 0) L.scale[dst >> 4] = cs.s;
+        inv = cs.inv;
+    }
+    static_cast<typename Codec<kCodec>::T*>(L.pool)[dst] = Codec<kCodec>::enc(f, inv);
 }
 
 // ---- layout -> per-cell lists ----------------------------------------------------
@@ -403,9 +414,8 @@ __global__ void k_gather(LayoutView L, const uint16_t* __restrict__ ids,
     int v = (int)(i & 63);
     int b = ids[t];
     const auto* pool = static_cast<const typename Codec<kCodec>::T*>(L.pool);
-    vals[i] = Codec<kCodec>::dec(
-        pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank_of[t]) * kChunk + (v & 15)],
-        kCodec ? L.scale[b] : 1.0f);
+    const int64_t e = ((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank_of[t]) * kChunk + (v & 15);
+    vals[i] = Codec<kCodec>::dec(pool[e], kCodec ? L.scale[e >> 4] : 1.0f);
 }
 
 // ---- moments -----------------------------------------------------------------------
@@ -447,9 +457,9 @@ __global__ void k_moments(GridGeom G, LayoutView L, VMesh V, double* __restrict_
                 for (int h = 0; h < 2; h++) {
                     int v = lane + 32 * h;
                     const auto* pool = static_cast<const typename Codec<kCodec>::T*>(L.pool);
-                    float f = Codec<kCodec>::dec(
-                        pool[((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15)],
-                        kCodec ? L.scale[b] : 1.0f);
+                    const int64_t e =
+                        ((int64_t)L.base[b] * 4 + (int64_t)(v >> 4) * L.cnt[b] + rank) * kChunk + (v & 15);
+                    float f = Codec<kCodec>::dec(pool[e], kCodec ? L.scale[e >> 4] : 1.0f);
                     double vel[3] = {V.vmin[0] + (bx * 4 + (v & 3) + 0.5) * V.dv[0],
                                      V.vmin[1] + (by * 4 + ((v >> 2) & 3) + 0.5) * V.dv[1],
                                      V.vmin[2] + (bz * 4 + (v >> 4) + 0.5) * V.dv[2]};
@@ -483,43 +493,6 @@ __global__ void k_fill_f32(float* __restrict__ p, float v, int64_t n)
     if (i < n) p[i] = v;
 }
 
-// Largest |f| per block id of input blocks t0 .. t0+m-1 (64 values each), one warp per
-// block: two values per lane, a warp maximum, one atomic per block.
-__global__ void k_block_vmax(const uint16_t* __restrict__ ids, const float* __restrict__ vals,
-                             int64_t t0, int64_t m, unsigned* __restrict__ vmax)
-{
-    int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (t >= m) return;
-    float a = fmaxf(fabsf(vals[t * 64 + lane]), fabsf(vals[t * 64 + 32 + lane]));
-    unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(a));
-    // a plain read first: most blocks do not raise their id's maximum, and a stale read
-    // only costs an atomic that changes nothing
-    if (lane == 0 && u) {
-        unsigned* dst = &vmax[ids[t0 + t]];
-        if (u > *(volatile unsigned*)dst) atomicMax(dst, u);
-    }
-}
-
-// scale[b] = smallest power of two >= max |f| of block id b
-__global__ void k_scale_from_vmax(const unsigned* __restrict__ vmax, float* __restrict__ scale, int nb)
-{
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) scale[b] = pow2_at_least(__uint_as_float(vmax[b]));
-}
-
-// Next layout of a step with 16-bit storage: scale from the current layout's maxima,
-// maxima of the next layout cleared (the step's last sweep accumulates them).
-__global__ void k_out_scale(const unsigned* __restrict__ vmax_cur, float* __restrict__ scale_next,
-                            unsigned* __restrict__ vmax_next, int nb, const int* abort)
-{
-    if (aborted(abort)) return;
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) {
-        scale_next[b] = pow2_at_least(__uint_as_float(vmax_cur[b]));
-        vmax_next[b] = 0u;
-    }
-}
 
 __global__ void k_popcount(const uint64_t* __restrict__ u, uint32_t* __restrict__ c, int64_t n)
 {
@@ -574,14 +547,8 @@ vl_status layout_alloc_meta(Grid* g, Layout& L)
     L.base = (int64_t*)g->alloc(((size_t)G.nb + 1) * 8);
     L.dense = (uint8_t*)g->alloc((size_t)G.nb);
     L.kcnt = (uint32_t*)g->alloc((size_t)G.nb * 4);
-    L.scale = (float*)g->alloc((size_t)G.nb * 4);
-    L.vmax = (unsigned*)g->alloc((size_t)G.nb * 4);
-    if (!L.ubits || !L.kbits || !L.woff || !L.wcount || !L.cnt || !L.base || !L.dense || !L.kcnt ||
-        !L.scale || !L.vmax)
+    if (!L.ubits || !L.kbits || !L.woff || !L.wcount || !L.cnt || !L.base || !L.dense || !L.kcnt)
         return fail(g, VL_ENOMEM, "allocation of the block bitmaps failed");
-    k_fill_f32<<<nblk(G.nb, 256), 256, 0, g->stream>>>(L.scale, 1.0f, G.nb);
-    note_launch();
-    cudaMemsetAsync(L.vmax, 0, (size_t)G.nb * 4, g->stream);
     cudaMemsetAsync(L.ubits, 0, words * 8, g->stream);
     cudaMemsetAsync(L.kbits, 0, words * 8, g->stream);
     cudaMemsetAsync(L.dense, 0, (size_t)G.nb, g->stream);
@@ -599,7 +566,6 @@ void layout_free(Grid* g, Layout& L)
     g->release(L.dense);
     g->release(L.kcnt);
     g->release(L.scale);
-    g->release(L.vmax);
     g->release(L.pool);
     g->release(L.keepq);
     L = Layout{};
@@ -610,8 +576,10 @@ void layout_release_pool(Grid* g, Layout& L)
     cudaStreamSynchronize(g->stream);  // no queued kernel may still use the pool
     g->release(L.pool);
     g->release(L.keepq);
+    g->release(L.scale);
     L.pool = nullptr;
     L.keepq = nullptr;
+    L.scale = nullptr;
     L.capacity = 0;
 }
 
@@ -621,9 +589,12 @@ vl_status layout_ensure_pool(Grid* g, Layout& L, int64_t blocks)
     int64_t cap = blocks + blocks / 32 + 64;
     g->release(L.pool);
     g->release(L.keepq);
+    g->release(L.scale);
     L.pool = g->alloc((size_t)cap * 64 * g->esize);
     L.keepq = (uint8_t*)g->alloc((size_t)cap * 4);
-    if (!L.pool || !L.keepq) {
+    // 16-bit storage: one power-of-two scale per chunk of 16 values
+    L.scale = g->codec ? (float*)g->alloc((size_t)cap * 4 * sizeof(float)) : nullptr;
+    if (!L.pool || !L.keepq || (g->codec && !L.scale)) {
         L.capacity = 0;
         return fail(g, VL_ENOMEM, "allocation of the phase-space pool failed (" +
                                       std::to_string(cap * 64 * (int64_t)g->esize) + " bytes)");
@@ -645,19 +616,26 @@ vl_status layout_grow_pool(Grid* g, Layout& L, int64_t blocks)
     if (blocks <= L.capacity && L.pool) return VL_OK;
     void* pool = g->alloc((size_t)blocks * 64 * g->esize);
     uint8_t* keepq = (uint8_t*)g->alloc((size_t)blocks * 4);
-    if (!pool || !keepq) {
+    float* scale = g->codec ? (float*)g->alloc((size_t)blocks * 4 * sizeof(float)) : nullptr;
+    if (!pool || !keepq || (g->codec && !scale)) {
         g->release(pool);
         g->release(keepq);
+        g->release(scale);
         return fail(g, VL_ENOMEM, "growing the phase-space pool failed (" + std::to_string(blocks * 64 * (int64_t)g->esize) + " bytes)");
     }
-    if (L.pool && L.total > 0)
-        cudaMemcpyAsync(pool, L.pool, (size_t)std::min(L.total, L.capacity) * 64 * g->esize,
-                        cudaMemcpyDeviceToDevice, g->stream);
+    if (L.pool && L.total > 0) {
+        const int64_t kept = std::min(L.total, L.capacity);
+        cudaMemcpyAsync(pool, L.pool, (size_t)kept * 64 * g->esize, cudaMemcpyDeviceToDevice, g->stream);
+        if (scale && L.scale)
+            cudaMemcpyAsync(scale, L.scale, (size_t)kept * 4 * sizeof(float), cudaMemcpyDeviceToDevice, g->stream);
+    }
     cudaStreamSynchronize(g->stream);
     g->release(L.pool);
     g->release(L.keepq);
+    g->release(L.scale);
     L.pool = pool;
     L.keepq = keepq;
+    L.scale = scale;
     L.capacity = blocks;
     return VL_OK;
 }
@@ -696,13 +674,6 @@ void launch_pack_keep(Grid* g, Layout& next, StepCounters* ctr)
     note_launch();
 }
 
-void launch_out_scale(Grid* g, const Layout& cur, Layout& next)
-{
-    if (g->codec == 0) return;
-    const GridGeom& G = g->geom;
-    k_out_scale<<<nblk(G.nb, 256), 256, 0, g->stream>>>(cur.vmax, next.scale, next.vmax, G.nb, G.abort);
-    note_launch();
-}
 
 namespace {
 struct Scratch {
@@ -739,8 +710,7 @@ static void* mapped_host(const void* p)
 }
 
 vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* ids_in,
-                     const float* vals_in, int on_device, const float* scale_host,
-                     const unsigned* vmax_host)
+                     const float* vals_in, int on_device)
 {
     const GridGeom& G = g->geom;
     cudaStream_t s = g->stream;
@@ -787,17 +757,6 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     k_dense_k<<<nblk(G.nb, 256), 256, 0, s>>>(L.cnt, L.dense, G.nb, G.N, nullptr, nullptr); note_launch();
     st = layout_ensure_pool(g, L, std::max<int64_t>(M, 1));
     if (st != VL_OK) return st;
-    // 16-bit storage: the scale of each block id (largest |f| of the input) comes first,
-    // unless given
-    cudaMemsetAsync(L.vmax, 0, (size_t)G.nb * 4, s);
-    const bool given = scale_host && vmax_host;
-    if (given) {
-        cudaMemcpyAsync(L.scale, scale_host, (size_t)G.nb * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(L.vmax, vmax_host, (size_t)G.nb * 4, cudaMemcpyHostToDevice, s);
-    } else if (g->codec == 0) {
-        k_fill_f32<<<nblk(G.nb, 256), 256, 0, s>>>(L.scale, 1.0f, G.nb);
-        note_launch();
-    }
     const int64_t chunk = std::min<int64_t>(std::max<int64_t>(M, 1), (int64_t)1 << 22);  // 1 GiB of values
     // host values: copied in chunks (the device never holds a second full copy) through
     // two staging buffers on a copy stream, so that the copy of one chunk overlaps the
@@ -806,9 +765,8 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
     cudaEvent_t ready = nullptr, copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
     const bool staged = M > 0 && !on_device && !mapped;
     const bool direct = on_device || mapped;  // the kernels read vals in place
-    const int npass = (g->codec && !given) ? 2 : 1;
-    // two buffers when more than one chunk goes through them (over both passes)
-    const int nbuf = (npass * ((M + chunk - 1) / chunk) > 1) ? 2 : 1;
+    // two buffers when more than one chunk goes through them
+    const int nbuf = ((M + chunk - 1) / chunk > 1) ? 2 : 1;
     if (staged) {
         for (int i = 0; i < nbuf; i++) {
             stage_buf[i] = (float*)sc.get((size_t)chunk * 256);
@@ -826,33 +784,23 @@ vl_status set_blocks(Grid* g, int64_t M, const int64_t* off_in, const uint16_t* 
         cudaEventRecord(ready, s);  // the staging buffers are free for the copy stream
         cudaStreamWaitEvent(g->copy_stream, ready, 0);
     }
-    int64_t k = 0;  // chunk counter over both passes (staging buffer k % nbuf)
-    for (int pass = (g->codec && !given ? 0 : 1); pass < 2 && M > 0; pass++) {
-        for (int64_t t0 = 0; t0 < M; t0 += (direct ? M : chunk), k++) {
-            const int64_t m = direct ? M : std::min(chunk, M - t0);
-            const int bi = (int)(k % nbuf);
-            const float* v = direct ? vals : stage_buf[bi];
-            if (staged) {
-                if (k >= nbuf) cudaStreamWaitEvent(g->copy_stream, used[bi], 0);  // chunk k-nbuf consumed
-                cudaMemcpyAsync(stage_buf[bi], vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice,
-                                g->copy_stream);
-                cudaEventRecord(copied[bi], g->copy_stream);
-                cudaStreamWaitEvent(s, copied[bi], 0);
-            }
-            if (pass == 0) {
-                k_block_vmax<<<nblk(m * 32, 256), 256, 0, s>>>(ids, v, t0, m, L.vmax);
-            } else {
-                with_codec(g->codec, [&](auto c) {
-                    k_scatter<decltype(c)::value><<<nblk(m * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, v, t0, m);
-                });
-            }
-            note_launch();
-            if (staged) cudaEventRecord(used[bi], s);
+    int64_t k = 0;  // chunk counter (staging buffer k % nbuf)
+    for (int64_t t0 = 0; t0 < M; t0 += (direct ? M : chunk), k++) {
+        const int64_t m = direct ? M : std::min(chunk, M - t0);
+        const int bi = (int)(k % nbuf);
+        const float* v = direct ? vals : stage_buf[bi];
+        if (staged) {
+            if (k >= nbuf) cudaStreamWaitEvent(g->copy_stream, used[bi], 0);  // chunk k-nbuf consumed
+            cudaMemcpyAsync(stage_buf[bi], vals_in + t0 * 64, (size_t)m * 256, cudaMemcpyHostToDevice,
+                            g->copy_stream);
+            cudaEventRecord(copied[bi], g->copy_stream);
+            cudaStreamWaitEvent(s, copied[bi], 0);
         }
-        if (pass == 0) {
-            k_scale_from_vmax<<<nblk(G.nb, 256), 256, 0, s>>>(L.vmax, L.scale, G.nb);
-            note_launch();
-        }
+        with_codec(g->codec, [&](auto c) {
+            k_scatter<decltype(c)::value><<<nblk(m * 64, 256), 256, 0, s>>>(G, L.view(), ids, cell_of, v, t0, m);
+        });
+        note_launch();
+        if (staged) cudaEventRecord(used[bi], s);
     }
     if (staged) {
         cudaStreamSynchronize(s);  // every copy was waited for by a kernel on s
@@ -1024,9 +972,9 @@ vl_status set_blocks_planes(Grid* g, int z0, int nplanes, int64_t Mw, const int6
         vals_w = c;
     }
     // fast path: the window keeps its block set (every listed block is present and the
-    // window holds as many), so the values go into their slots in place -- FP32 storage
-    // (16-bit codes may need new scales)
-    if (g->codec == 0) {
+    // window holds as many), so the values go into their slots in place (16-bit storage:
+    // with the chunk scales of the new values)
+    {
         const int origin[3] = {0, 0, z0};
         const int size[3] = {G.n[0], G.n[1], nplanes};
         int64_t Mcur = -1;
@@ -1049,7 +997,10 @@ vl_status set_blocks_planes(Grid* g, int z0, int nplanes, int64_t Mw, const int6
             if (herr & 2) return fail(g, VL_EINVAL, "vl_set_blocks_planes: block id out of range of the velocity mesh");
             if (herr == 0) {
                 if (Mw > 0) {
-                    k_scatter<0><<<nblk(Mw * 64, 256), 256, 0, s>>>(G, L.view(), ids_w, cell_of, vals_w, 0, Mw);
+                    with_codec(g->codec, [&](auto c) {
+                        k_scatter<decltype(c)::value>
+                            <<<nblk(Mw * 64, 256), 256, 0, s>>>(G, L.view(), ids_w, cell_of, vals_w, 0, Mw);
+                    });
                     note_launch();
                 }
                 e = cudaStreamSynchronize(s);

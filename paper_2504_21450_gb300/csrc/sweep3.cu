@@ -64,6 +64,11 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     __shared__ int s_rin[kPencils][kMaxLine];
     __shared__ int s_rout[kPencils][kMaxLine];
     __shared__ int s_any[kPencils];
+    // 16-bit storage: largest |new value| per (pencil, chunk, cell) as float bits,
+    // [kPencils][4][nd].  The velocity cells of a chunk may walk in opposite directions
+    // here (a block straddling v = 0), so a chunk's 16 new values appear at different
+    // times: a first walk finds their maximum, a second one encodes and stores.
+    extern __shared__ unsigned s_cmax[];
     const GridGeom& G = P.G;
     if (aborted(G.abort)) return;
     const int b = (int)(blockIdx.x / P.groups);
@@ -74,6 +79,8 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
 
     // ranks of every cell of the CTA's pencils in both layouts
     if (threadIdx.x < kPencils) s_any[threadIdx.x] = 0;
+    if constexpr (kCodec != 0)
+        for (int t = threadIdx.x; t < kPencils * 4 * nd; t += blockDim.x) s_cmax[t] = 0u;
     __syncthreads();
     for (int t = threadIdx.x; t < kPencils * nd; t += blockDim.x) {
         int k = t / nd, i = t - k * nd;
@@ -93,7 +100,10 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     __syncthreads();
     const int k = threadIdx.x >> 6;
     const int v = threadIdx.x & 63;
-    if (!s_any[k]) return;  // nothing of this pencil is in the next layout (warp-uniform)
+    // nothing of this pencil is in the next layout (warp-uniform); with 16-bit storage
+    // the pencil's threads stay for the CTA's barriers and skip the walks
+    const bool active = s_any[k] != 0;
+    if (kCodec == 0 && !active) return;
 
     const int q = v >> 4, l = v & 15;
     int bc[3] = {b % G.nbx, (b / G.nbx) % G.nby, b / (G.nbx * G.nby)};
@@ -104,38 +114,70 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
     // the warp's velocity cells move the same way unless the block straddles v_d = 0
     const bool uni = __all_sync(0xffffffffu, up) || __all_sync(0xffffffffu, !up);
 
-    const T* src = static_cast<const T*>(P.in.pool) +
-                   ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + l;
-    T* dst = static_cast<T*>(P.out.pool) + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + l;
-    // 16-bit storage: scales of the codes read and written (passes 2 and 3 read the
-    // codes the previous pass wrote with the output scale)
-    const float sc_in = kCodec ? P.in.scale[b] : 1.0f;
-    const float sc_out = kCodec ? P.out.scale[b] : 1.0f;
-    const float inv_out = 1.0f / sc_out;  // a power of two: exact
+    // chunk indices of cell rank 0 of this chunk row in both layouts (16-bit storage
+    // keeps one scale per chunk, indexed like the chunks)
+    const int64_t cin = (int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b];
+    const int64_t cout = (int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b];
+    const T* src = static_cast<const T*>(P.in.pool) + cin * kChunk + l;
+    T* dst = static_cast<T*>(P.out.pool) + cout * kChunk + l;
     const int* rin = s_rin[k];
     const int* rout = s_rout[k];
+    unsigned* cmax = s_cmax + (k * 4 + q) * nd;
     // the walk runs from the upwind end: walking position m is cell m (c >= 0) or
     // cell nd-1-m (c < 0)
     auto cell_at = [&](int m) { return up ? m : nd - 1 - m; };
     auto load = [&](int m) -> float {
         int r = rin[cell_at(m)];
-        return r >= 0 ? C::dec(src[(int64_t)r * kChunk], sc_in) : 0.0f;
+        return r >= 0 ? C::dec(src[(int64_t)r * kChunk], kCodec ? P.in.scale[cin + r] : 1.0f) : 0.0f;
     };
-    // originals of walking positions 0 and 1, read again by the wrapped tail after
-    // they were updated in place
-    const float t0 = load(0), t1 = load(1 % nd);
-
-    Walk<kLim> s;
-    s.reset();
     float msum = 0.0f;
-    float vmx = 0.0f;  // largest |stored value| (16-bit storage, last pass)
     double mass = 0.0;
+    // one walk over the pencil calling emit(mm, res) with the new average of every
+    // walking position mm
+    auto walk = [&](auto emit) {
+        // originals of walking positions 0 and 1, read again by the wrapped tail after
+        // they were updated in place
+        const float t0 = load(0), t1 = load(1 % nd);
+        Walk<kLim> s;
+        s.reset();
+        int m = -3;
+        for (; m < 0; m++) s.push(load(wrapi(m, nd)), kc);
+        // main walk, loads batched ahead of the dependent arithmetic
+        for (; m + 8 <= nd; m += 8) {
+            float a[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) a[u] = load(m + u);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                float res = s.push(a[u], kc);
+                if (m + u >= 2) emit(m + u - 2, res);
+            }
+            mass += (double)msum;
+            msum = 0.0f;
+        }
+        for (; m < nd; m++) {
+            float res = s.push(load(m), kc);
+            if (m >= 2) emit(m - 2, res);
+        }
+        const float tail[2] = {t0, t1};
+#pragma unroll
+        for (int u = 0; u < 2; u++, m++) {
+            float res = s.push(tail[u], kc);
+            if (m >= 2) emit(m - 2, res);
+        }
+    };
     const float thr = P.thr;
     auto emit = [&](int mm, float res) {  // new average of walking position mm
         int c = cell_at(mm);
         int r = rout[c];
-        const T code = C::enc(res, inv_out);
-        if (kCodec) res = C::dec(code, sc_out);  // the value the state now holds
+        T code;
+        if constexpr (kCodec != 0) {
+            const ChunkScale cs = chunk_scale(__uint_as_float(cmax[c]));
+            code = C::enc(res, cs.inv);
+            res = C::dec(code, cs.s);  // the value the state now holds
+        } else {
+            code = res;
+        }
         if (r >= 0) dst[(int64_t)r * kChunk] = code;
         if (P.last) {
             bool keep = r >= 0 && res >= thr;
@@ -147,47 +189,36 @@ __global__ void __launch_bounds__(kThreads3) k_pass(PassArgs P)
             } else if (keep) {
                 *kq = 1;
             }
-            if (r >= 0) {
-                msum += res;
-                if (kCodec) vmx = fmaxf(vmx, fabsf(res));
-            }
+            if (r >= 0) msum += res;
         }
     };
-    int m = -3;
-    for (; m < 0; m++) s.push(load(wrapi(m, nd)), kc);
-    // main walk, loads batched ahead of the dependent arithmetic
-    for (; m + 8 <= nd; m += 8) {
-        float a[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) a[u] = load(m + u);
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            float res = s.push(a[u], kc);
-            if (m + u >= 2) emit(m + u - 2, res);
+    if constexpr (kCodec != 0) {
+        if (active)
+            walk([&](int mm, float res) {
+                const int c = cell_at(mm);
+                if (rout[c] >= 0) atomicMax(&cmax[c], __float_as_uint(fabsf(res)));
+            });
+        __syncthreads();  // every chunk's maximum is complete
+        // the second walk reads the codes with the scales they were written with (in
+        // place: the new scales replace them only after it)
+        if (active) walk(emit);
+        __syncthreads();
+        for (int t = threadIdx.x; t < kPencils * 4 * nd; t += blockDim.x) {
+            const int kk = t / (4 * nd), rem = t - kk * 4 * nd;
+            const int qq = rem / nd, c = rem - qq * nd;
+            const int r = s_rout[kk][c];
+            if (r >= 0)
+                P.out.scale[(int64_t)P.out.base[b] * 4 + (int64_t)qq * P.out.cnt[b] + r] =
+                    chunk_scale(__uint_as_float(s_cmax[t])).s;
         }
-        if (P.last) {
-            mass += (double)msum;
-            msum = 0.0f;
-        }
-    }
-    for (; m < nd; m++) {
-        float res = s.push(load(m), kc);
-        if (m >= 2) emit(m - 2, res);
-    }
-    const float tail[2] = {t0, t1};
-#pragma unroll
-    for (int u = 0; u < 2; u++, m++) {
-        float res = s.push(tail[u], kc);
-        if (m >= 2) emit(m - 2, res);
+        if (!active) return;
+    } else {
+        walk(emit);
     }
     if (P.last) {
         mass += (double)msum;
         for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
         if ((threadIdx.x & 31) == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
-        if (kCodec) {
-            unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
-            if ((threadIdx.x & 31) == 0 && u) atomicMax(&P.out.vmax[b], u);
-        }
     }
 }
 
@@ -235,7 +266,8 @@ __device__ __forceinline__ void store4(typename Codec<kCodec>::T* p, const typen
     }
 }
 
-template <bool kLim, int kCodec>
+// kLast: the last pass (keep flags and mass, which need the values the state now holds)
+template <bool kLim, int kCodec, bool kLast>
 __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
 {
     using C = Codec<kCodec>;
@@ -289,19 +321,17 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
     const WalkConst2 kp[2] = {pack_const(kc[0], kc[1]), pack_const(kc[2], kc[3])};
     const bool uni = __all_sync(0xffffffffu, up) || __all_sync(0xffffffffu, !up);
 
-    const T* src = static_cast<const T*>(P.in.pool) +
-                   ((int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b]) * kChunk + 4 * vy;
-    T* dst = static_cast<T*>(P.out.pool) + ((int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b]) * kChunk + 4 * vy;
-    const float sc_in = kCodec ? P.in.scale[b] : 1.0f;
-    const float sc_out = kCodec ? P.out.scale[b] : 1.0f;
-    const float inv_out = 1.0f / sc_out;
+    const int64_t cin = (int64_t)P.in.base[b] * 4 + (int64_t)q * P.in.cnt[b];    // chunk of rank 0
+    const int64_t cout = (int64_t)P.out.base[b] * 4 + (int64_t)q * P.out.cnt[b];
+    const T* src = static_cast<const T*>(P.in.pool) + cin * kChunk + 4 * vy;
+    T* dst = static_cast<T*>(P.out.pool) + cout * kChunk + 4 * vy;
     const int* rin = s_rin + k * nd;
     const int* rout = s_rout + k * nd;
     auto cell_at = [&](int m) { return up ? m : nd - 1 - m; };
     auto load = [&](int m, float (&o)[4]) {
         const int r = rin[cell_at(m)];
         if (r >= 0) {
-            load4<kCodec>(src + (int64_t)r * kChunk, sc_in, o);
+            load4<kCodec>(src + (int64_t)r * kChunk, kCodec ? P.in.scale[cin + r] : 1.0f, o);
         } else {
             o[0] = o[1] = o[2] = o[3] = 0.0f;
         }
@@ -314,9 +344,11 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
     s[0].reset();
     s[1].reset();
     float msum = 0.0f;
-    float vmx = 0.0f;
     double mass = 0.0;
     const float thr = P.thr;
+    // every lane calls it for the same position; the 4 lanes of a chunk (one vx row each)
+    // are consecutive, and in place they have all read the chunk at position m - 2 before
+    // the shuffles of that position's call, so its scale may be replaced
     auto push_emit = [&](int m, const float (&a)[4]) {
         float res[4];
         const float2 r01 = s[0].push(make_float2(a[0], a[1]), kp[0]);
@@ -329,13 +361,21 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
         const int c = cell_at(m - 2);
         const int r = rout[c];
         T code[4];
+        if constexpr (kCodec != 0) {
+            const float mx = fmaxf(fmaxf(fabsf(res[0]), fabsf(res[1])), fmaxf(fabsf(res[2]), fabsf(res[3])));
+            const ChunkScale cs = chunk_scale(group_max<4>(mx));
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            code[i] = C::enc(res[i], inv_out);
-            if (kCodec) res[i] = C::dec(code[i], sc_out);
+            for (int i = 0; i < 4; i++) {
+                code[i] = C::enc(res[i], cs.inv);
+                if constexpr (kLast) res[i] = C::dec(code[i], cs.s);  // the value the state now holds
+            }
+            if (r >= 0 && vy == 0) P.out.scale[cout + r] = cs.s;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++) code[i] = res[i];
         }
         if (r >= 0) store4<kCodec>(dst + (int64_t)r * kChunk, code);
-        if (P.last) {
+        if constexpr (kLast) {
             const bool keep = r >= 0 && (res[0] >= thr || res[1] >= thr || res[2] >= thr || res[3] >= thr);
             uint8_t* kq = P.keepq + ((int64_t)P.out.base[b] + r) * 4 + q;
             if (uni) {
@@ -345,10 +385,7 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
             } else if (keep) {
                 *kq = 1;
             }
-            if (r >= 0) {
-                msum += (res[0] + res[1]) + (res[2] + res[3]);
-                if (kCodec) vmx = fmaxf(vmx, fmaxf(fmaxf(fabsf(res[0]), fabsf(res[1])), fmaxf(fabsf(res[2]), fabsf(res[3]))));
-            }
+            if (r >= 0) msum += (res[0] + res[1]) + (res[2] + res[3]);
         }
     };
     int m = -3;
@@ -380,7 +417,7 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
         }
 #pragma unroll
         for (int u = 0; u < kBatch4; u++) push_emit(m + u, a[u]);
-        if (P.last) {
+        if constexpr (kLast) {
             mass += (double)msum;
             msum = 0.0f;
         }
@@ -392,14 +429,10 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
     }
     push_emit(m, t0);
     push_emit(m + 1, t1);
-    if (P.last) {
+    if constexpr (kLast) {
         mass += (double)msum;
         for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
         if ((threadIdx.x & 31) == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
-        if (kCodec) {
-            unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(vmx));
-            if ((threadIdx.x & 31) == 0 && u) atomicMax(&P.out.vmax[b], u);
-        }
     }
 }
 
@@ -432,13 +465,16 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         P.ctr = a.ctr;
         int64_t npen = G.N / G.n[d];
         // the vector kernel needs one walking direction per vx row: along x, no block
-        // may straddle v_x = 0
+        // may straddle v_x = 0.  With 16-bit storage the four rows of a chunk must also
+        // walk together (they share the chunk's scale), which along y needs the same
         bool vec = true;
-        if (d == 0)
-            for (int bx = 0; bx < G.nbx && vec; bx++) {
-                const double lo = P.vmin + (4 * bx + 0.5) * P.dv, hi = P.vmin + (4 * bx + 3.5) * P.dv;
+        if (d == 0 || (d == 1 && g->codec)) {
+            const int nbd = d == 0 ? G.nbx : G.nby;
+            for (int bi = 0; bi < nbd && vec; bi++) {
+                const double lo = P.vmin + (4 * bi + 0.5) * P.dv, hi = P.vmin + (4 * bi + 3.5) * P.dv;
                 if ((lo >= 0.0) != (hi >= 0.0)) vec = false;
             }
+        }
         const int per_cta = vec ? kPen4 : kPencils;
         P.groups = (npen + per_cta - 1) / per_cta;
         int64_t nblocks = P.groups * G.nb;
@@ -447,13 +483,16 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         with_codec(g->codec, [&](auto c) {
             constexpr int kc = decltype(c)::value;
             if (vec) {
-                auto kern = a.limiter ? k_pass4<true, kc> : k_pass4<false, kc>;
+                auto kern = a.limiter ? (P.last ? k_pass4<true, kc, true> : k_pass4<true, kc, false>)
+                                      : (P.last ? k_pass4<false, kc, true> : k_pass4<false, kc, false>);
                 if (smem4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4);
                 kern<<<(unsigned)nblocks, kThreads4, smem4, g->stream>>>(P);
-            } else if (a.limiter) {
-                k_pass<true, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
             } else {
-                k_pass<false, kc><<<(unsigned)nblocks, kThreads3, 0, g->stream>>>(P);
+                auto kern = a.limiter ? k_pass<true, kc> : k_pass<false, kc>;
+                // 16-bit storage: per-chunk maxima of the pencils
+                const int smem = kc ? kPencils * 4 * G.n[d] * (int)sizeof(unsigned) : 0;
+                if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                kern<<<(unsigned)nblocks, kThreads3, smem, g->stream>>>(P);
             }
         });
         note_launch();

@@ -123,8 +123,8 @@ def test_batched_captured_steps_equal_step_by_step():
 
 def test_default_kernel_and_where_it_does_not_apply():
     """The default fused kernel is the plane-batched one where it applies; blocks that
-    straddle v = 0, an x-last order or 16-bit storage fall back to the row-segment
-    kernel, and asking for the plane-batched kernel there is VL_EINVAL."""
+    straddle v = 0 or an x-last order fall back to the row-segment kernel, and asking
+    for the plane-batched kernel there is VL_EINVAL."""
     n = (21, 14, 9)
     init = inputs.random_blocks(n, (8, 8, 8), 0.4, seed=94)
     ok = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
@@ -150,8 +150,9 @@ def test_default_kernel_and_where_it_does_not_apply():
 @pytest.mark.parametrize("order", ["xyz", "yxz"])
 def test_batched_16bit_storage_equals_row_segment_kernel(storage, order):
     """Scaled 16-bit storage: both fused kernels decode the stored codes, run the same
-    per-velocity-cell arithmetic in FP32 and round once per step with the same scale,
-    so their states, codes included, agree bit for bit; sparse blocks and pruning."""
+    per-velocity-cell arithmetic in FP32 and round once per step, each chunk with the
+    scale of its own new values, so their states, codes included, agree bit for bit;
+    sparse blocks and pruning."""
     n = (37, 19, 11)
     init = inputs.random_blocks(n, (8, 8, 8), 0.35, seed=96)
     mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
@@ -166,4 +167,4 @@ def test_batched_16bit_storage_equals_row_segment_kernel(storage, order):
         g.close()
     for x, y in zip(outs[0][0], outs[1][0]):
         np.testing.assert_array_equal(x, y)
-    assert outs[0][1] == outs[1][1]  # checkpoints: codes, scales and maxima
+    assert outs[0][1] == outs[1][1]  # checkpoints
