@@ -65,9 +65,11 @@ struct Gt3Smem {
     int pref;                 // batch 0 of the current item was staged during the last one
     int abort;
 };
-// 16-bit storage: the chunk scales of the staged cells, [2][kNB][kE * kE] floats after
-// Gt3Smem (per batch buffer and plane, staged row-major like the cells)
-constexpr int kScales = 2 * kNB * kE * kE;
+// 16-bit storage: the chunk scales of the staged cells, [2][kNB][kE][kSP] floats after
+// Gt3Smem (per batch buffer and plane, staged row-major like the cells).  The row pitch
+// is odd, so that the staging threads, one per row, write 32 different banks.
+constexpr int kSP = kE + 1;
+constexpr int kScales = 2 * kNB * kE * kSP;
 template <int kCodec>
 constexpr size_t smem_bytes() { return sizeof(Gt3Smem) + (kCodec ? kScales * sizeof(float) : 0); }
 __device__ __forceinline__ float* scales_of(Gt3Smem& S) { return reinterpret_cast<float*>(&S + 1); }
@@ -312,7 +314,7 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
             const int pz = wrapi(plane_of(kNB * k + j), n2);
             const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
             float* drow = &S.buf[slot][j][rho * kRP];
-            float* srow = scales_of(S) + ((slot * kNB + j) * kE + rho) * kE;
+            float* srow = scales_of(S) + ((slot * kNB + j) * kE + rho) * kSP;
             if constexpr (kA0X) {
                 float* codes = drow + (it.up0 ? kCodesHi : 0);
                 fence_async_smem();
@@ -499,8 +501,8 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
     constexpr int kS0 = kA0X ? kChunk : kRP;
     constexpr int kS1 = kA0X ? kRP : kChunk;
     // the same for the scale table (one float per staged cell)
-    constexpr int kC0 = kA0X ? 1 : kE;
-    constexpr int kC1 = kA0X ? kE : 1;
+    constexpr int kC0 = kA0X ? 1 : kSP;
+    constexpr int kC1 = kA0X ? kSP : 1;
 
     if (tid == 0) {
         // FP32: one arrival (with the batch's bytes); 16-bit: one per staging thread
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
                     const WalkConst2 kx{make_float2(c0.x, c1.x), make_float2(c0.y, c1.y), make_float2(c0.z, c1.z)};
                     float* p = B + j * kPS + (line + (up1 ? 0 : 1)) * kS1 + l0;
                     // 16-bit storage: chunk scales of the line's cells
-                    const float* ps = scales_of(S) + (slot * kNB + j) * kE * kE + (line + (up1 ? 0 : 1)) * kC1;
+                    const float* ps = scales_of(S) + (slot * kNB + j) * kE * kSP + (line + (up1 ? 0 : 1)) * kC1;
                     // the two staged values of position m: FP32, or two 16-bit codes in the
                     // upper half of the cell's slot
                     // packed codes of the line (sweep 0 along x), see stage_batch

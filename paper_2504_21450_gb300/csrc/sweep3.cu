@@ -268,7 +268,7 @@ __device__ __forceinline__ void store4(typename Codec<kCodec>::T* p, const typen
 
 // kLast: the last pass (keep flags and mass, which need the values the state now holds)
 template <bool kLim, int kCodec, bool kLast>
-__global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
+__global__ void __launch_bounds__(kThreads4, 2) k_pass4(PassArgs P)
 {
     using C = Codec<kCodec>;
     using T = typename C::T;
@@ -395,31 +395,71 @@ __global__ void __launch_bounds__(kThreads4) k_pass4(PassArgs P)
         s[0].push(make_float2(a[0], a[1]), kp[0]);
         s[1].push(make_float2(a[2], a[3]), kp[1]);
     }
-    for (; m + kBatch4 <= nd; m += kBatch4) {
-        float a[kBatch4][4];
+    if constexpr (kCodec == 0) {
+        for (; m + kBatch4 <= nd; m += kBatch4) {
+            float a[kBatch4][4];
 #pragma unroll
-        for (int u = 0; u < kBatch4; u++) load(m + u, a[u]);
-        // L2 prefetch of the next batch (one lane per chunk row): DRAM keeps working
-        // while this batch's arithmetic runs, and the next loads hit L2.  It takes no
-        // registers; a distance of one batch measured best (FP32: 0.88 of the copy
-        // bandwidth against 0.76 without, 0.85 at two batches).  16-bit storage moves
-        // half the bytes and is issue-bound, where the extra instructions cost more
-        // than the overlap gains (46.9 against 44.4 ms per step), so it goes without.
-        if (kCodec == 0 && vy == 0) {
+            for (int u = 0; u < kBatch4; u++) load(m + u, a[u]);
+            // L2 prefetch of the next batch (one lane per chunk row): DRAM keeps working
+            // while this batch's arithmetic runs, and the next loads hit L2.  It takes no
+            // registers; a distance of one batch measured best (0.88 of the copy
+            // bandwidth against 0.76 without, 0.85 at two batches).
+            if (vy == 0) {
 #pragma unroll
-            for (int u = 0; u < kBatch4; u++) {
-                const int pm = m + kBatch4 + u;
-                if (pm < nd) {
-                    const int r = rin[cell_at(pm)];
-                    if (r >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (int64_t)r * kChunk));
+                for (int u = 0; u < kBatch4; u++) {
+                    const int pm = m + kBatch4 + u;
+                    if (pm < nd) {
+                        const int r = rin[cell_at(pm)];
+                        if (r >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (int64_t)r * kChunk));
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kBatch4; u++) push_emit(m + u, a[u]);
-        if constexpr (kLast) {
-            mass += (double)msum;
-            msum = 0.0f;
+            for (int u = 0; u < kBatch4; u++) push_emit(m + u, a[u]);
+            if constexpr (kLast) {
+                mass += (double)msum;
+                msum = 0.0f;
+            }
+        }
+    } else {
+        // 16-bit storage: the batch is held as raw codes and scales (3 registers per
+        // position instead of 4) and decoded as it is pushed; the next batch's code
+        // sectors and scales are prefetched into L2 like the FP32 rows (50.4 against 64.3
+        // ms per bfloat16 step without; batches of 12 positions measured 52.6 ms)
+        for (; m + kBatch4 <= nd; m += kBatch4) {
+            uint2 raw[kBatch4];
+            float sc[kBatch4];
+#pragma unroll
+            for (int u = 0; u < kBatch4; u++) {
+                const int r = rin[cell_at(m + u)];
+                raw[u] = r >= 0 ? *reinterpret_cast<const uint2*>(src + (int64_t)r * kChunk) : make_uint2(0u, 0u);
+                sc[u] = r >= 0 ? P.in.scale[cin + r] : 0.0f;
+            }
+            if (vy == 0) {
+#pragma unroll
+                for (int u = 0; u < kBatch4; u++) {
+                    const int pm = m + kBatch4 + u;
+                    if (pm < nd) {
+                        const int r = rin[cell_at(pm)];
+                        if (r >= 0) {
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (int64_t)r * kChunk));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(P.in.scale + cin + r));
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch4; u++) {
+                float a[4];
+                const T* h = reinterpret_cast<const T*>(&raw[u]);
+#pragma unroll
+                for (int i = 0; i < 4; i++) a[i] = C::dec(h[i], sc[u]);
+                push_emit(m + u, a);
+            }
+            if constexpr (kLast) {
+                mass += (double)msum;
+                msum = 0.0f;
+            }
         }
     }
     for (; m < nd; m++) {
