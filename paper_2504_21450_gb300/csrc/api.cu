@@ -264,7 +264,7 @@ vl_status translate_graph(Grid* g, StepArgs a, bool fused, int nsteps, int64_t c
         if (g->lay[g->cur].capacity < cap) layout_release_pool(g, g->lay[1 - g->cur]);
         st = layout_grow_pool(g, g->lay[g->cur], cap);
         if (st == VL_OK) st = layout_ensure_pool(g, g->lay[1 - g->cur], cap);
-        if (st == VL_OK && fused) st = fused_worklist_alloc(g, a);
+        if (st == VL_OK) st = fused ? fused_worklist_alloc(g, a) : pass_worklist_alloc(g);
         if (st == VL_OK && g->step_ctr_n < n) {
             g->release(g->step_ctr);
             if (g->step_ctr_host) cudaFreeHost(g->step_ctr_host);

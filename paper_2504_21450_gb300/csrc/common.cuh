@@ -361,7 +361,8 @@ struct StepCounters {
     double dropped_mass;   // sum over removed blocks
     unsigned long long kept;
     unsigned long long dropped;
-    unsigned long long work_next;  // persistent-kernel work counter
+    unsigned long long work_next;  // persistent-kernel work counter (fused form)
+    unsigned long long pass_next[3];  // work counters of the three passes (3-pass form)
     int error;                     // bit 2: staging wait ran out; bit 3: capacity overflow
     int done;                      // 1 once every kernel of the step has run
     long long needed;              // slots the step's union needed (capacity checks)

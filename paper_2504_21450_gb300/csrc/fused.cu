@@ -736,16 +736,18 @@ __global__ void k_tile_flags(TileArgs T, uint32_t* __restrict__ flags)
     flags[i] = any ? 1u : 0u;
 }
 
+// flat: the item is the pair's index b * ntiles + tile itself (the caller needs no
+// search of item_base to find b)
 __global__ void k_tile_items(int64_t ntiles, int nb, const uint32_t* __restrict__ flags,
                              const uint32_t* __restrict__ pos, const int64_t* __restrict__ base,
-                             uint32_t* __restrict__ items, const int* abort)
+                             uint32_t* __restrict__ items, int flat, const int* abort)
 {
     if (aborted(abort)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)nb * ntiles) return;
     if (!flags[i]) return;
     int b = (int)(i / ntiles);
-    items[base[b] + pos[i]] = (uint32_t)(i - (int64_t)b * ntiles);
+    items[base[b] + pos[i]] = (uint32_t)(flat ? i : i - (int64_t)b * ntiles);
 }
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -773,17 +775,47 @@ vl_status launch_fused(Grid* g, const FusedArgs& P)
 
 }  // namespace
 
+// Compaction of g->tile_flags ([nb][ntiles] 0/1) into the work list: items[item_base[b]
+// .. item_base[b+1]) = the flagged tiles of block id b in ascending order (flat: as
+// b * ntiles + tile).
+void launch_items_from_flags(Grid* g, int64_t ntiles, bool flat)
+{
+    const GridGeom& G = g->geom;
+    const int64_t need = ntiles * G.nb;
+    launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, G.nb, g->stream, G.abort);
+    launch_base_scan(g->item_cnt, g->item_base, G.nb, g->stream, G.abort);
+    k_tile_items<<<nblk(need, 256), 256, 0, g->stream>>>(ntiles, G.nb, g->tile_flags, g->tile_pos,
+                                                           g->item_base, g->items, flat ? 1 : 0, G.abort);
+    note_launch();
+}
+
 // Work list of a fused launch: one item per (block id, tile column) holding any slot of
 // the next layout, grouped by block id (item_base[b] .. item_base[b+1]).
 void launch_tile_list(Grid* g, const TileArgs& T, int64_t need, int64_t ntiles)
 {
     k_tile_flags<<<nblk(need, 256), 256, 0, g->stream>>>(T, g->tile_flags);
     note_launch();
-    launch_seg_scan(g->tile_flags, g->tile_pos, g->item_cnt, ntiles, T.G.nb, g->stream, T.G.abort);
-    launch_base_scan(g->item_cnt, g->item_base, T.G.nb, g->stream, T.G.abort);
-    k_tile_items<<<nblk(need, 256), 256, 0, g->stream>>>(ntiles, T.G.nb, g->tile_flags, g->tile_pos,
-                                                           g->item_base, g->items, T.G.abort);
-    note_launch();
+    launch_items_from_flags(g, ntiles, false);
+}
+
+// Work-list buffers for `need` (block id, tile) pairs (allocated before any captured
+// step sequence; they never shrink).
+vl_status worklist_reserve(Grid* g, int64_t need)
+{
+    if (need > 0xffffffffLL) return fail(g, VL_EINVAL, "work list: more than 2^32 (block id, tile) pairs");
+    if (need <= g->ntiles_alloc) return VL_OK;
+    g->release(g->tile_flags);
+    g->release(g->tile_pos);
+    g->release(g->items);
+    g->tile_flags = (uint32_t*)g->alloc((size_t)need * 4);
+    g->tile_pos = (uint32_t*)g->alloc((size_t)need * 4);
+    g->items = (uint32_t*)g->alloc((size_t)need * 4);
+    if (!g->tile_flags || !g->tile_pos || !g->items) {
+        g->ntiles_alloc = 0;
+        return fail(g, VL_ENOMEM, "work-list allocation failed");
+    }
+    g->ntiles_alloc = need;
+    return VL_OK;
 }
 
 // Work-list buffers of the fused form for this sweep order (allocated before any
@@ -797,20 +829,7 @@ vl_status fused_worklist_alloc(Grid* g, const StepArgs& a)
     const GridGeom& G = g->geom;
     const int ty = tile_rows(a);
     const int64_t ntiles = (int64_t)((G.n[a.order[0]] + TX - 1) / TX) * ((G.n[a.order[1]] + ty - 1) / ty);
-    const int64_t need = ntiles * G.nb;
-    if (need <= g->ntiles_alloc) return VL_OK;
-    g->release(g->tile_flags);
-    g->release(g->tile_pos);
-    g->release(g->items);
-    g->tile_flags = (uint32_t*)g->alloc((size_t)need * 4);
-    g->tile_pos = (uint32_t*)g->alloc((size_t)need * 4);
-    g->items = (uint32_t*)g->alloc((size_t)need * 4);
-    if (!g->tile_flags || !g->tile_pos || !g->items) {
-        g->ntiles_alloc = 0;
-        return fail(g, VL_ENOMEM, "fused form: work-list allocation failed");
-    }
-    g->ntiles_alloc = need;
-    return VL_OK;
+    return worklist_reserve(g, ntiles * G.nb);
 }
 
 vl_status run_fused(Grid* g, const StepArgs& a)

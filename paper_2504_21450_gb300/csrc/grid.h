@@ -208,6 +208,13 @@ inline bool use_gt3(const Grid* g, const StepArgs& a)
     return gt3_applies(g, a);
 }
 vl_status fused_worklist_alloc(Grid* g, const StepArgs& a);
+// Work-list buffers (g->tile_flags, tile_pos, items) for `need` (block id, tile) pairs.
+vl_status worklist_reserve(Grid* g, int64_t need);
+// Compacts g->tile_flags ([nb][ntiles]) into g->items / g->item_base (flat: items hold
+// b * ntiles + tile).
+void launch_items_from_flags(Grid* g, int64_t ntiles, bool flat);
+// Work-list buffers of the 3-pass form (its pencil groups; before any captured sequence).
+vl_status pass_worklist_alloc(Grid* g);
 int tile_rows(const StepArgs& a);
 vl_status run_fused(Grid* g, const StepArgs& a);
 vl_status run_3pass(Grid* g, const StepArgs& a);
