@@ -73,11 +73,17 @@ typedef enum {
     VL_FORM_FUSED = 0,  /* Ghost Translation: one tile+halo load, x->y->z in one kernel */
     VL_FORM_3PASS = 1,  /* classical: one HBM round trip per sweep direction */
     VL_FORM_AUTO = 2    /* pick per workload: the first steps run for a workload probe
-                           each candidate -- fused with 16-row tiles (orders ending in z),
-                           fused with 8-row tiles, 3-pass (FP32 storage only) -- with one
-                           warm-up and one timed step each, over as many calls as it takes
-                           (every probe step advances the real state; the candidates
-                           compute the same result).  The fastest is cached per workload
+                           each candidate -- fused with the plane-batched kernel (where it
+                           applies), fused row-segment kernel with 16-row tiles (orders
+                           ending in z) and with 8-row tiles, 3-pass (FP32 storage only) --
+                           with one warm-up and one timed step each, over as many calls as
+                           it takes (every probe step advances the real state; the
+                           candidates compute the same result).  With FP32 storage a prior
+                           from Section 3.3's ghost-work count rules out, unprobed, a fused
+                           candidate whose tile sweeps more than 3 times as many cells per
+                           useful update as the 3-pass form (it moves a third of the bytes,
+                           so it cannot win); a single remaining candidate is taken
+                           without probing.  The fastest is cached per workload
                            key (grid, velocity mesh, order, limiter, storage, slots per
                            cell rounded to a power of two); with the environment variable
                            VLGT_TUNE_CACHE naming a file the choices also persist across
@@ -167,7 +173,8 @@ typedef struct {
     int tile_rows_used;     /* fused form: tile rows along the second sweep axis */
     double tune_ms[4];      /* autotuner probes (ms per step): fused plane-batched kernel,
                                fused row-segment kernel with 16-row and 8-row tiles,
-                               3-pass; 0 = not probed */
+                               3-pass; 0 = not applicable, -1 = ruled out by the
+                               ghost-work prior (VL_FORM_AUTO) */
     int64_t updates;        /* phase-space cell updates of the call: velocity cells present
                                at the start of each step, summed over its steps */
     double tail_ms;         /* fused steps run one by one: summed over steps, the time from

@@ -418,6 +418,42 @@ uint64_t tune_key(const Grid* g, const StepArgs& a)
     return k;
 }
 
+// Section 3.3's trade-off as a prior: PPM pushes per useful cell update of a fused
+// candidate over those of the 3-pass form on this grid.  A fused tile sweeps its halo
+// too (the ghost cells the coalesced update brings in), so its pushes per useful update
+// grow as the grid shrinks below the tile; the 3-pass form pays a 5-push ramp per
+// pencil.  The fused form moves a third of the 3-pass bytes, so a candidate that pushes
+// more than 3 times as often cannot win, even against a 3-pass step bound by memory
+// alone, and is not probed.  Counts per streamed plane of one tile of the kernels:
+//   plane-batched, 16 x 16 tiles: sweep 0 on 21 lines x 21 positions, sweep 1 on 16
+//     lines x 21, sweep 2 on 16 x 16 cells; n2 + 5 planes per item;
+//   row-segment, 16 x TY tiles: sweep 0 on TY+6 rows x 21, sweep 1 on 16 columns x two
+//     segments of TY/2 + 5, sweep 2 on 16 x TY; n2 + 5 planes (n2 + 6 unless the streamed
+//     axis is z).
+constexpr double kPriorTraffic = 3.0;
+
+double prior_ratio(const Grid* g, const StepArgs& a, int kernel, int ty)
+{
+    const int* n = g->geom.n;
+    const int n0 = n[a.order[0]], n1 = n[a.order[1]], n2 = n[a.order[2]];
+    double per_plane, planes;
+    int rows;
+    if (kernel == 1) {
+        rows = 16;
+        per_plane = 21.0 * 21.0 + 16.0 * 21.0 + 16.0 * 16.0;
+        planes = n2 + 5.0;
+    } else {
+        rows = ty;
+        per_plane = (ty + 6.0) * 21.0 + 16.0 * 2.0 * (ty / 2 + 5.0) + 16.0 * ty;
+        planes = n2 + (a.order[2] == 2 ? 5.0 : 6.0);
+    }
+    const double tiles = (double)((n0 + 15) / 16) * (double)((n1 + rows - 1) / rows);
+    const double fused = tiles * per_plane * planes / ((double)n0 * n1 * n2);
+    double classical = 0.0;
+    for (int d = 0; d < 3; d++) classical += (n[d] + 5.0) / n[d];
+    return fused / classical;
+}
+
 void tune_load_locked()
 {
     if (g_tune_loaded) return;
@@ -900,20 +936,45 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 pr = g_tune_progress[key];
             }
+            // which candidates run: the plane-batched kernel where it applies; 16-row
+            // tiles of the row-segment kernel need a z-last order; with 16-bit storage the
+            // 3-pass form rounds to storage after every sweep, so it is not the same
+            // computation as the fused form and only the fused kernels are tuned; a fused
+            // candidate the prior rules out is not probed (tune_ms -1)
+            bool runs[kTuneCands];
+            int nrun = 0, last_run = -1;
+            for (int c = 0; c < kTuneCands; c++) {
+                StepArgs ac = a;
+                ac.tile[1] = cand_ty[c];
+                ac.kernel = cand_kernel[c];
+                runs[c] = !((cand_kernel[c] == 1 && !gt3_applies(g, ac)) ||
+                            (cand_kernel[c] == 2 && cand_ty[c] == 16 && a.order[2] != 2) ||
+                            (cand_form[c] == VL_FORM_3PASS && g->codec != 0));
+                if (runs[c] && cand_form[c] == VL_FORM_FUSED && g->codec == 0 &&
+                    prior_ratio(g, a, cand_kernel[c], cand_ty[c]) > kPriorTraffic) {
+                    runs[c] = false;
+                    pr.entry.ms[c] = -1.0;
+                }
+                if (runs[c]) {
+                    nrun++;
+                    last_run = c;
+                }
+            }
+            if (nrun == 1 && pr.cand == 0 && !pr.warmed) {
+                // one candidate left: nothing to compare
+                pr.entry.form = cand_form[last_run];
+                pr.entry.ty = cand_ty[last_run];
+                pr.entry.kernel = cand_kernel[last_run];
+                pr.cand = kTuneCands;
+            }
             // each candidate: one warm-up step, then one timed step, possibly over
             // several calls; every step advances the real state
             while (st == VL_OK && pr.cand < kTuneCands && done < nsteps) {
                 const int c = pr.cand;
-                // the plane-batched kernel where it applies; 16-row tiles of the
-                // row-segment kernel need a z-last order; with 16-bit storage the 3-pass
-                // form rounds to storage after every sweep, so it is not the same
-                // computation as the fused form and only the fused kernels are tuned
                 StepArgs ac = a;
                 ac.tile[1] = cand_ty[c];
                 ac.kernel = cand_kernel[c];
-                if ((cand_kernel[c] == 1 && !gt3_applies(g, ac)) ||
-                    (cand_kernel[c] == 2 && cand_ty[c] == 16 && a.order[2] != 2) ||
-                    (cand_form[c] == VL_FORM_3PASS && g->codec != 0)) {
+                if (!runs[c]) {
                     pr.cand++;
                     continue;
                 }

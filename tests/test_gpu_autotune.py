@@ -126,3 +126,21 @@ def test_plane_batched_kernel_is_probed_where_it_applies():
     assert s.form_used == (vlasov.VL_FORM_3PASS if best == 3 else vlasov.VL_FORM_FUSED)
     if best < 3:
         assert s.kernel_used == (1 if best == 0 else 2)
+
+
+def test_ghost_work_prior_rules_out_fused_tiles_on_a_small_grid():
+    """On an 8 x 8 x 8 grid a 16 x 16 tile sweeps its halo four times over for the cells it
+    updates (Section 3.3's ghost overhead growing as the domain shrinks): every fused
+    candidate pushes more than 3 times as often per useful update as the 3-pass form, so
+    the prior rules them out (tune_ms -1), the 3-pass form is taken unprobed (tune_ms 0),
+    and the state equals a fixed 3-pass run's.  On 40 x 33 x 18 every candidate is probed
+    (the tests above)."""
+    n = (8, 8, 8)
+    init = inputs.random_blocks(n, (8, 8, 8), 0.5, seed=73)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    ref, _ = run(mesh, init, 3, vlasov.VL_FORM_3PASS)
+    got, s = run(mesh, init, 3, vlasov.VL_FORM_AUTO)
+    assert list(s.tune_ms) == [-1.0, -1.0, -1.0, 0.0]
+    assert s.form_used == vlasov.VL_FORM_3PASS and s.steps == 3
+    for x, y in zip(ref, got):
+        np.testing.assert_array_equal(x, y)
