@@ -177,10 +177,12 @@ typedef struct {
                                ghost-work prior (VL_FORM_AUTO) */
     int64_t updates;        /* phase-space cell updates of the call: velocity cells present
                                at the start of each step, summed over its steps */
-    double tail_ms;         /* fused steps run one by one: summed over steps, the time from
-                               the first to the last CTA of the persistent sweep kernel
-                               running out of work (the single-GPU counterpart of the
-                               paper's wait time, Table 1); 0 otherwise */
+    double tail_ms;         /* steps run one by one: summed over steps, the time from the
+                               first to the last CTA of a persistent sweep kernel running
+                               out of work (the single-GPU counterpart of the paper's wait
+                               time, Table 1) -- the fused kernel, or the three passes of
+                               the 3-pass form on a sparse state (work-list mode); 0
+                               otherwise */
     int kernel_used;        /* fused form: 1 plane-batched kernel, 2 row-segment kernel */
     int reserved_stats;
 } vl_step_stats;

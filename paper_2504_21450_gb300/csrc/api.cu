@@ -168,15 +168,15 @@ vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_s
 {
     a.ev0 = g->ev_sweep0;
     a.ev1 = g->ev_sweep1;
-    // finish times of the fused kernel's CTAs (its idle tail, reported as tail_ms)
-    if (fused && !g->cta_done) {
+    // finish times of the persistent kernels' CTAs (their idle tail, reported as tail_ms)
+    if (!g->cta_done) {
         g->cta_done = (uint64_t*)g->alloc((size_t)kMaxCtas * 8);
         if (g->cta_done && cudaMallocHost((void**)&g->cta_done_host, (size_t)kMaxCtas * 8) != cudaSuccess) {
             cudaGetLastError();
             g->cta_done_host = nullptr;
         }
     }
-    a.stamp_ctas = fused && g->cta_done && g->cta_done_host;
+    a.stamp_ctas = g->cta_done && g->cta_done_host;
     cudaEvent_t e0, e1, ep;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -190,8 +190,10 @@ vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_s
         cudaMemcpyAsync(g->counters_host, g->counters, sizeof(StepCounters), cudaMemcpyDeviceToHost,
                         g->stream);
         const int nct = a.stamp_ctas ? g->cta_count : 0;
+        const int ngr = nct > 0 ? g->cta_groups : 0;
         if (nct > 0)
-            cudaMemcpyAsync(g->cta_done_host, g->cta_done, (size_t)nct * 8, cudaMemcpyDeviceToHost, g->stream);
+            cudaMemcpyAsync(g->cta_done_host, g->cta_done, (size_t)nct * ngr * 8, cudaMemcpyDeviceToHost,
+                            g->stream);
         cudaError_t e = cudaStreamSynchronize(g->stream);
         if (e != cudaSuccess) {
             st = cuda_fail(g, e, "vl_translate step");
@@ -206,9 +208,9 @@ vl_status translate_steps(Grid* g, StepArgs a, bool fused, int nsteps, vl_step_s
         S->index_ms += ms;
         cudaEventElapsedTime(&ms, g->ev_sweep1, e1);
         S->prune_ms += ms;
-        if (nct > 0) {
+        for (int k = 0; k < ngr; k++) {
             uint64_t lo = ~0ull, hi = 0;
-            for (int c = 0; c < nct; c++) {
+            for (int c = k * nct; c < (k + 1) * nct; c++) {
                 lo = std::min(lo, g->cta_done_host[c]);
                 hi = std::max(hi, g->cta_done_host[c]);
             }

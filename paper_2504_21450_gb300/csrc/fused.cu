@@ -766,6 +766,7 @@ vl_status launch_fused(Grid* g, const FusedArgs& P)
     const int nct = nsm * per_sm;
     if (nct > kMaxCtas) Q.cta_done = nullptr;
     g->cta_count = Q.cta_done ? nct : 0;
+    g->cta_groups = 1;
     kern<<<nct, NT, smem, g->stream>>>(Q);
     note_launch();
     cudaError_t e = cudaGetLastError();

@@ -73,7 +73,8 @@ struct Grid {
     cudaStream_t copy_stream = nullptr;   // host-to-device staging of vl_set_blocks
     uint64_t* cta_done = nullptr;         // device [kMaxCtas]: finish time of each fused CTA
     uint64_t* cta_done_host = nullptr;    // pinned copy
-    int cta_count = 0;                    // CTAs of the last fused launch
+    int cta_count = 0;                    // CTAs of the last stamped launch
+    int cta_groups = 1;                   // launches stamped back to back (3-pass: three passes)
     float4* ctab = nullptr;               // device [2][3][nvmax] sweep constants
     float4* ctab_host = nullptr;          // pinned staging of the same
     double ctab_dt = -1.0;                // dt the table was built for
@@ -149,7 +150,7 @@ struct StepArgs {
     int nvmax;
     StepCounters* ctr;    // counters of this step
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the sweep kernels when set
-    bool stamp_ctas = false;  // fused kernel: each CTA records when it ran out of work
+    bool stamp_ctas = false;  // persistent kernels: each CTA records when it ran out of work
     int kernel = 0;       // fused form: 0 plane-batched where it applies and no row-segment
                           // tile is asked for (tile[1]), else row-segment; 1 plane-batched
                           // (VL_EINVAL where it does not apply); 2 row-segment

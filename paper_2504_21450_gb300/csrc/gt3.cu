@@ -768,6 +768,7 @@ vl_status launch_gt3(Grid* g, const Gt3Args& P)
     Gt3Args Q = P;
     if (nsm > kMaxCtas) Q.cta_done = nullptr;
     g->cta_count = Q.cta_done ? nsm : 0;
+    g->cta_groups = 1;
     kern<<<nsm, kNT, smem_bytes<kCodec>(), g->stream>>>(Q);
     note_launch();
     cudaError_t e = cudaGetLastError();

@@ -44,6 +44,7 @@ struct PassArgs {
     const uint32_t* items;
     const int64_t* item_base;
     unsigned long long* next;
+    uint64_t* cta_done;  // optional, list mode [gridDim.x]: %globaltimer when the CTA ran out of work
 };
 
 // physical coordinates of pencil p, position i along dim
@@ -584,6 +585,11 @@ __global__ void __launch_bounds__(kThreads4, 2) k_pass4(PassArgs P)
         for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
         if (lane == 0 && mass != 0.0) atomicAdd(&P.ctr->mass, mass);
     }
+    if (kList && P.cta_done && threadIdx.x == 0) {
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+        P.cta_done[blockIdx.x] = t;
+    }
 }
 
 }  // namespace
@@ -607,6 +613,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
             return fail(g, VL_EINVAL, "3-pass form: grid extent above 1024 cells");
     vl_status wst = pass_worklist_alloc(g);
     if (wst != VL_OK) return wst;
+    int stamped[3] = {0, 0, 0};  // CTAs of each pass that stamp their finish time
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev.device);
     record_sweep_event(a.ev0, g->stream, a.ev_node);
@@ -629,6 +636,7 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         P.items = nullptr;
         P.item_base = nullptr;
         P.next = &a.ctr->pass_next[j];
+        P.cta_done = nullptr;
         int64_t npen = G.N / G.n[d];
         // the vector kernel needs one walking direction per vx row: along x, no block
         // may straddle v_x = 0.  With 16-bit storage the four rows of a chunk must also
@@ -673,6 +681,12 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
                 int per_sm = 0;
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads4, smem4);
                 const int64_t nct = listed ? std::min<int64_t>(nblocks, (int64_t)nsm * std::max(per_sm, 1)) : nblocks;
+                // each pass of a listed step stamps its CTAs into its own third of the
+                // array (the idle tail of the persistent grid, reported as tail_ms)
+                if (listed && a.stamp_ctas && 3 * nct <= kMaxCtas) {
+                    P.cta_done = g->cta_done + j * nct;
+                    stamped[j] = (int)nct;
+                }
                 kern<<<(unsigned)nct, kThreads4, smem4, g->stream>>>(P);
             } else {
                 auto kern = a.limiter ? k_pass<true, kc> : k_pass<false, kc>;
@@ -685,6 +699,10 @@ vl_status run_3pass(Grid* g, const StepArgs& a)
         note_launch();
     }
     record_sweep_event(a.ev1, g->stream, a.ev_node);
+    // tails are reported when every pass stamped (all three listed, equal grids)
+    const bool all = stamped[0] > 0 && stamped[0] == stamped[1] && stamped[1] == stamped[2];
+    g->cta_count = all ? stamped[0] : 0;
+    g->cta_groups = all ? 3 : 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(g, e, "3-pass sweep launch");
     return VL_OK;
