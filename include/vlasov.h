@@ -285,8 +285,9 @@ vl_status vl_stats(vl_grid* grid, vl_step_stats* stats);
 /* One translation step that allocates no device memory.
  *
  * The paper has no counterpart to this call: it exists for callers that cannot allocate,
- * such as code running inside a CUDA graph capture region, a runtime that owns the whole
- * device memory budget, or an embedding host whose allocator this library cannot reach.
+ * such as a runtime that owns the whole device memory budget, an embedding host whose
+ * allocator this library cannot reach, or code that must not touch the device heap
+ * between two steps.
  *
  * It runs the fused Ghost Translation kernel (the three PPM sweeps, Section 3) once on a
  * DENSE velocity space (every cell holds every block id), without the sparsity rule.
