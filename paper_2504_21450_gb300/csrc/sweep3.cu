@@ -4,12 +4,15 @@
 // contribution, Section 2.1 / Fig. 1).
 //
 // Pass 1 reads the current layout (present blocks only) and writes every slot of the
-// next layout (the 27-cell union); passes 2 and 3 update the next layout in place.  One
-// thread walks one periodic pencil for one velocity cell with the sliding-window PPM
-// remap (Walk, from the upwind end of the pencil); the 64 threads of a block id cover
-// its 64 velocity cells, so every step of a walk is a coalesced load of 2 x 64 bytes
-// per warp.  The last pass also raises the per-chunk keep flags of the sparsity rule
-// (set-only: the flags are cleared before the step) and sums the mass.
+// next layout (the 27-cell union); passes 2 and 3 update the next layout in place.  A
+// walk runs along one periodic pencil from its upwind end with the sliding-window PPM
+// remap.  The vector kernel (k_pass4) gives a thread one vx row of a velocity chunk
+// (four walks as two packed pairs, 16-byte accesses) and a CTA item 16 pencils of one
+// block id: one CTA per (block id, pencil group) on a dense state, a persistent grid over
+// a device-built list of the non-empty pairs on a sparse one.  The scalar kernel (k_pass)
+// gives a thread one velocity cell, for blocks whose cells walk in both directions.  The
+// last pass also raises the per-chunk keep flags of the sparsity rule (set-only: the
+// flags are cleared before the step) and sums the mass.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
