@@ -362,3 +362,38 @@ def test_page_locked_host_buffers_are_read_and_written_in_place(storage):
     np.testing.assert_array_equal(o_vals.numpy(), want[2])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n, density, storage", [
+    ((1024, 2, 1), 1.0, vlasov.VL_STORE_F32),    # dense: one CTA per pencil group
+    ((1024, 2, 1), 0.3, vlasov.VL_STORE_F32),    # sparse: work list, persistent passes
+    ((2, 1, 1024), 0.3, vlasov.VL_STORE_F32),    # the longest pencil along z
+    ((1024, 1, 2), 0.3, vlasov.VL_STORE_F16_SCALED),
+])
+def test_longest_pencils(n, density, storage):
+    """Pencils of 1024 cells, the longest the 3-pass form holds in shared memory (its rank
+    tables and slot bitmaps, one CTA per SM), in both forms against the oracle; a grid
+    one cell longer is rejected by the 3-pass form with VL_EINVAL."""
+    init = inputs.random_blocks(n, (8, 8, 8), density, seed=49)
+    mesh = oracle.Mesh(n=n, nv=(8, 8, 8), vmin=(-4.0,) * 3, dv=(1.0,) * 3)
+    f32 = storage == vlasov.VL_STORE_F32
+    # 16-bit storage: no pruning (a block near the threshold may round across it), and
+    # the rounding of up to three sweeps (values below 1, so normal float16 codes)
+    thr, tol = (0.1, VAL_TOL) if f32 else (0.0, 4 * 2.0 ** -11)
+    for form in FORMS.values():
+        g = vlasov.Grid(mesh.n, mesh.nv, mesh.vmin, mesh.dv, mesh.dx, threshold=thr, storage=storage)
+        g.set_blocks(init.off, init.ids, init.vals)
+        off, ids, vals = g.get_blocks()
+        before = oracle.as_blocks(off, ids, vals.astype(np.float64))
+        g.translate(0.2, "xyz", 1, form, check=True)
+        err, fmax, amb, _, _ = compare_step(mesh, before, g.get_blocks(), thr, 0.2, "xyz")
+        assert err <= tol * fmax, (form, err, fmax)
+        g.close()
+    longer = tuple(c + 1 if c == 1024 else c for c in n)
+    init = inputs.random_blocks(longer, (8, 8, 8), density, seed=49)
+    g = vlasov.Grid(longer, (8, 8, 8), (-4.0,) * 3, (1.0,) * 3, (1.0,) * 3, threshold=thr, storage=storage)
+    g.set_blocks(init.off, init.ids, init.vals)
+    with pytest.raises(vlasov.VlError) as e:
+        g.translate(0.2, "xyz", 1, vlasov.VL_FORM_3PASS, check=True)
+    assert e.value.status == vlasov.VL_EINVAL
+    g.close()
