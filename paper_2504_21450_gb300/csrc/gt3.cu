@@ -663,7 +663,15 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
             // the in-place writes of this batch precede the bulk copies that refill the
             // buffer two batches on
             fence_async_smem();
-            __syncthreads();  // sweep 1 complete
+            // sweep 1 complete.  The sweep-1 warps do not wait for the staging warps, whose
+            // bulk-copy issue can outlast sweep 1: they arrive on barrier 2 and wait among
+            // themselves (barrier 3); the staging warps wait on barrier 2 for them
+            if (stager) {
+                asm volatile("bar.sync 2, %0;\n" ::"n"(kNC) : "memory");
+            } else {
+                asm volatile("bar.arrive 2, %0;\n" ::"n"(kNC) : "memory");
+                asm volatile("bar.sync 3, %0;\n" ::"n"(kNY) : "memory");
+            }
             // sweep 2: push the batch's planes through the streamed windows and emit
             auto zplane = [&](int j) {
                 const int s = kNB * k + j;
