@@ -100,11 +100,6 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(bar)), "r"(bytes)
-                 : "memory");
-}
 __device__ __forceinline__ void bar_add_tx(uint64_t* bar, unsigned bytes)
 {
     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(bytes)
@@ -281,16 +276,29 @@ __device__ __forceinline__ void item_tables(const Gt3Args& P, Gt3Smem& S, const 
 }
 
 // Staging of batch k of an item (planes kNB k .. kNB k + 2 of its stream) into buffer
-// g & 1, g = the CTA's running batch index; run by the kNS staging threads (sl = 0..127).
-// FP32 storage: TMA bulk copies of contiguous runs.  16-bit storage: one staging thread
-// per staged row, and every staging thread arrives on the barrier once its copies have
-// landed.  The chunk scale of each staged cell goes into the scale table with a 4-byte
+// g & 1, g = the CTA's running batch index; run by the kNS staging threads (sl = 0..127),
+// one staged row per thread, and every staging thread arrives on the batch's barrier
+// once its copies have landed.  Contiguous runs of a row go by TMA bulk copies; the short
+// run where a dense row wraps around the periodic grid (kShortRun cells or fewer) goes by
+// 16-byte cp.async copies instead: the SM's bulk-copy unit takes a roughly fixed time per
+// request, and these runs would add half as many requests again.  The chunk scale of each staged cell goes into the scale table with a 4-byte
 // cp.async copy (0 for an absent cell).  With sweep 0 along x the row's codes are packed
 // at one end of the row (kCodesHi) by bulk copies per contiguous run: sweep 0 walks
 // towards that end and writes its FP32 result two cells behind the one it reads, which
 // overwrites only codes read at least three positions earlier.  Otherwise the 32 bytes of
 // codes of each cell go to the upper half of its own 64-byte slot with two 16-byte
 // cp.async copies, so that each line of sweep 0 overwrites only codes it has read.
+constexpr int kShortRun = 4;
+
+// cells of an item's staged row that go by bulk copies (runs longer than kShortRun)
+__device__ __forceinline__ int bulk_cells(const Gt3Smem& S, int t)
+{
+    int c = 0;
+    for (int k2 = 0; k2 < S.nrun[t]; k2++)
+        if (S.run[t][k2][2] > kShortRun) c += S.run[t][k2][2];
+    return c;
+}
+
 template <int kCodec, bool kA0X>
 __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const Item& it, int t, int k,
                                             unsigned g, int sl)
@@ -302,6 +310,9 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
     uint64_t* bar = &S.bar[slot];
     const int nj = min(kNB, nsteps - kNB * k);
     const int nrun = S.nrun[t];
+    // staged row (and output row) of this thread: rows go round-robin over the four
+    // staging warps, whose lanes issue their copies one after another
+    const int sw = (sl & 31) * (kNS / 32) + (sl >> 5);
     const float* ipool = static_cast<const float*>(P.in.pool);
     auto plane_of = [&](int s) { return it.up2 ? s - kHalo : n2 + 2 - s; };
     auto out_of = [&](int s) { return it.up2 ? s - kFirst : n2 + 4 - s; };
@@ -309,8 +320,8 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
         using T = typename Codec<kCodec>::T;
         const T* cpool = static_cast<const T*>(P.in.pool) + it.ibase;  // codes of rank 0
         const float* spool = P.in.scale + it.ibase / kChunk;            // scale of rank 0
-        if (sl < nj * kE) {
-            const int j = sl / kE, rho = sl - j * kE;
+        if (sw < nj * kE) {
+            const int j = sw / kE, rho = sw - j * kE;
             const int pz = wrapi(plane_of(kNB * k + j), n2);
             const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
             float* drow = &S.buf[slot][j][rho * kRP];
@@ -320,9 +331,16 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
                 fence_async_smem();
                 if (it.dense_in) {
                     const int64_t r0 = row * nx;
-                    for (int k2 = 0; k2 < nrun; k2++)
-                        copy_g2s(codes + S.run[t][k2][0] * (kChunk / 2), cpool + (r0 + S.run[t][k2][1]) * kChunk,
-                                 (unsigned)(S.run[t][k2][2] * kChunk * sizeof(T)), bar);
+                    for (int k2 = 0; k2 < nrun; k2++) {
+                        const int u0 = S.run[t][k2][0], x0 = S.run[t][k2][1], len = S.run[t][k2][2];
+                        float* d = codes + u0 * (kChunk / 2);
+                        const T* src = cpool + (r0 + x0) * kChunk;
+                        if (len > kShortRun) {
+                            copy_g2s(d, src, (unsigned)(len * kChunk * sizeof(T)), bar);
+                        } else {
+                            for (int i = 0; i < len * 2; i++) cp16(d + 4 * i, src + 8 * i, 16);
+                        }
+                    }
                     for (int u = 0; u < kE; u++) cp4(srow + u, spool + r0 + S.xs[t][u], 4);
                 } else {
                     // runs of present cells (consecutive slots) as bulk copies, each announced
@@ -387,29 +405,39 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
         }
         // dense rows with sweep 0 along x: the batch's code bytes, announced without an
         // arrival (the phase also waits for every staging thread's arrival below)
-        if (kA0X && it.dense_in && sl == 0) bar_add_tx(bar, (unsigned)(nj * kE * kE * kChunk * sizeof(T)));
+        if (kA0X && it.dense_in && sl == 0)
+            bar_add_tx(bar, (unsigned)(nj * kE * bulk_cells(S, t) * kChunk * sizeof(T)));
         cp_arrive(bar);
     } else if (it.dense_in) {
-        // one arrival carrying the batch's bytes; the copies of the other staging
-        // threads may complete before or after it
-        if (sl == 0) bar_arrive_tx(bar, (unsigned)(nj * kE * kE * kChunk * sizeof(float)));
-        if (sl < nj * kE) {
-            const int j = sl / kE, rho = sl - j * kE;
+        // the batch's bulk-copy bytes, announced once (the copies of the other staging
+        // threads may complete before or after it; the phase also waits for every staging
+        // thread's arrival)
+        if (sl == 0) bar_add_tx(bar, (unsigned)(nj * kE * bulk_cells(S, t) * kChunk * sizeof(float)));
+        if (sw < nj * kE) {
+            const int j = sw / kE, rho = sw - j * kE;
             const int pz = wrapi(plane_of(kNB * k + j), n2);
             const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
             const float* src = ipool + it.ibase + row * nx * kChunk;
             float* dst = &S.buf[slot][j][rho * kRP];
             fence_async_smem();
-            for (int k2 = 0; k2 < nrun; k2++)
-                copy_g2s(dst + S.run[t][k2][0] * kChunk, src + S.run[t][k2][1] * kChunk,
-                         (unsigned)(S.run[t][k2][2] * kChunk * sizeof(float)), bar);
+            for (int k2 = 0; k2 < nrun; k2++) {
+                const int u0 = S.run[t][k2][0], x0 = S.run[t][k2][1], len = S.run[t][k2][2];
+                if (len > kShortRun) {
+                    copy_g2s(dst + u0 * kChunk, src + x0 * kChunk, (unsigned)(len * kChunk * sizeof(float)), bar);
+                } else {
+                    for (int i = 0; i < len * (kChunk / 4); i++)
+                        cp16(dst + u0 * kChunk + 4 * i, src + x0 * kChunk + 4 * i, 16);
+                }
+            }
         }
+        cp_arrive(bar);
     } else {
         // runs of present cells (consecutive slots) as bulk copies, each announced to the
-        // barrier before it is issued; absent cells are zeroed.  The one arrival comes
-        // after every staging thread has announced its bytes.
-        if (sl < nj * kE) {
-            const int j = sl / kE, rho = sl - j * kE;
+        // barrier before it is issued; absent cells are zeroed.  Each staging thread
+        // arrives after announcing its bytes, so the phase cannot end before every
+        // announcement.
+        if (sw < nj * kE) {
+            const int j = sw / kE, rho = sw - j * kE;
             const int pz = wrapi(plane_of(kNB * k + j), n2);
             const int64_t row = (int64_t)S.rrow[t][rho] + rowpart(a2, pz, ny);
             const int64_t wbase = (int64_t)it.b * G.RW + row * G.W;
@@ -452,12 +480,11 @@ __device__ __forceinline__ void stage_batch(const Gt3Args& P, Gt3Smem& S, const 
                 }
             }
         }
-        asm volatile("bar.sync 1, %0;\n" ::"n"(kNS) : "memory");
-        if (sl == 0) bar_arrive(bar);
+        bar_arrive(bar);
     }
     // output slots of the tile cells of a sparse next layout
-    if (!it.dense_out && sl < nj * kT) {
-        const int j = sl / kT, rr = sl - j * kT;
+    if (!it.dense_out && sw < nj * kT) {
+        const int j = sw / kT, rr = sw - j * kT;
         const int s = kNB * k + j;
         if (s >= kFirst) {
             const int zo = out_of(s);
@@ -505,9 +532,9 @@ __global__ void __launch_bounds__(kNT, 1) k_gt3(Gt3Args P)
     constexpr int kC1 = kA0X ? kSP : 1;
 
     if (tid == 0) {
-        // FP32: one arrival (with the batch's bytes); 16-bit: one per staging thread
-        bar_init(&S.bar[0], kCodec ? kNS : 1);
-        bar_init(&S.bar[1], kCodec ? kNS : 1);
+        // one arrival per staging thread
+        bar_init(&S.bar[0], kNS);
+        bar_init(&S.bar[1], kNS);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         S.abort = 0;
         S.pref = 0;
