@@ -83,7 +83,11 @@ typedef enum {
                            candidate whose tile sweeps more than 3 times as many cells per
                            useful update as the 3-pass form (it moves a third of the bytes,
                            so it cannot win); a single remaining candidate is taken
-                           without probing.  The fastest is cached per workload
+                           without probing.  Candidates are compared by the time of their
+                           sweep kernels per updated cell in the timed step (the other
+                           phases are the same for all of them, and a step that grows a
+                           pool spends host time that says nothing about the form); the
+                           fastest is cached per workload
                            key (grid, velocity mesh, order, limiter, storage, slots per
                            cell rounded to a power of two); with the environment variable
                            VLGT_TUNE_CACHE naming a file the choices also persist across
@@ -171,7 +175,8 @@ typedef struct {
     int64_t capacity;       /* graph mode: blocks per layout at the end of the call */
     int form_used;          /* vl_form of the last step (after autotuning) */
     int tile_rows_used;     /* fused form: tile rows along the second sweep axis */
-    double tune_ms[4];      /* autotuner probes (ms per step): fused plane-batched kernel,
+    double tune_ms[4];      /* autotuner probes (sweep kernels' ms in the timed probe
+                               step): fused plane-batched kernel,
                                fused row-segment kernel with 16-row and 8-row tiles,
                                3-pass; 0 = not applicable, -1 = ruled out by the
                                ghost-work prior (VL_FORM_AUTO) */

@@ -1003,9 +1003,14 @@ vl_status vl_translate(vl_grid* grid, double dt, const char* order, int nsteps,
                     pr.warmed = true;
                     continue;
                 }
-                pr.entry.ms[c] = probe.device_ms;
-                if (probe.device_ms < pr.best) {
-                    pr.best = probe.device_ms;
+                // candidates are compared by their sweep kernels' time per update: the
+                // union, index and sparsity phases are the same for every candidate; a step
+                // that grows a pool (the union outgrew it) spends host time inside the step
+                // that says nothing about the form; and the state moves between probes
+                pr.entry.ms[c] = probe.sweep_ms;
+                const double per_update = probe.sweep_ms / (double)std::max<int64_t>(probe.updates, 1);
+                if (per_update < pr.best) {
+                    pr.best = per_update;
                     pr.entry.form = cand_form[c];
                     pr.entry.ty = cand_ty[c];
                     pr.entry.kernel = cand_kernel[c];
