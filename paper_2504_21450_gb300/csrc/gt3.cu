@@ -7,9 +7,11 @@
 // per step, and all three sweeps run on it.  What differs is how the work is laid out on
 // the SM:
 //   * planes are processed in batches of three.  While the CTA sweeps batch k, the four
-//     warps that sit out sweep 1 stage batch k+1 with TMA bulk copies (one per contiguous
-//     run of a halo row), and the CTA synchronises twice per batch instead of twice per
-//     plane;
+//     warps that sit out sweep 1 stage batch k+1, one halo row per thread, with TMA bulk
+//     copies (one per contiguous run of a row; 16-byte cp.async for the short run where a
+//     dense row wraps around the periodic grid).  The CTA synchronises once per batch
+//     after sweep 0; after sweep 1 the sweep-1 warps only arrive on a named barrier that
+//     the staging warps wait on, and go on to sweep 2 among themselves;
 //   * every walk moves two velocity cells in packed f32x2 registers: sweep 0 runs on the
 //     21 halo lines that sweep 1 reads (3 planes x 21 lines x 8 lane pairs = 504 walks),
 //     sweep 1 on the 16 tile lines (384 walks), both in place in shared memory;
